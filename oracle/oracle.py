@@ -1,0 +1,220 @@
+"""ctypes front end of the FP64 CPU oracle (tdbem_oracle.c).
+
+TEST INFRASTRUCTURE: only the test suite, `__graft_entry__.smoke()` and the
+CPU-baseline leg of `bench.py` import this module. It never imports the CUDA
+package, and the CUDA package never imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tdbem_oracle.c")
+_LIB = os.path.join(_HERE, "_tdbem_oracle.so")
+_lib = None
+
+f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp) next to its source."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.or_create.restype = C.c_void_p
+        L.or_create.argtypes = [f64p, C.c_int64, i32p, C.c_int64, f64p, C.c_int64,
+                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.or_destroy.argtypes = [C.c_void_p]
+        L.or_num_blocks.restype = C.c_int64
+        L.or_num_blocks.argtypes = [C.c_void_p]
+        L.or_block.argtypes = [C.c_void_p, C.c_int64, i32p, f64p]
+        L.or_diam.restype = C.c_double
+        L.or_diam.argtypes = [C.c_void_p]
+        L.or_tri_geom.argtypes = [C.c_void_p, C.c_int64, f64p]
+        L.or_set_first_kind.argtypes = [C.c_void_p, C.c_int]
+        L.or_basis.argtypes = [C.c_void_p, C.c_int, C.c_int, f64p, C.c_int64, f64p]
+        L.or_mu.argtypes = [C.c_void_p, C.c_int, f64p, C.c_int64, f64p]
+        L.or_psi.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, f64p, C.c_int64, f64p]
+        L.or_psi_block.argtypes = [C.c_void_p, C.c_int64, f64p, C.c_int64, f64p]
+        L.or_tri_bounds.argtypes = [C.c_void_p, C.c_int64, C.c_int64, f64p]
+        L.or_rule7.argtypes = [f64p, f64p]
+        L.or_ss_rule.restype = C.c_int64
+        L.or_ss_rule.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.or_gauss_legendre.argtypes = [C.c_int, f64p, f64p]
+        L.or_pair_local.argtypes = [C.c_void_p, C.c_int64, C.c_int64, i64p, C.c_int, C.c_int, C.c_int, f64p]
+        L.or_pattern_counts.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64, i64p]
+        L.or_assemble_rows.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64, i64p, i32p, f64p, f64p]
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def gauss_legendre(n):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().or_gauss_legendre(n, x, w)
+    return x, w
+
+
+def rule7():
+    b = np.zeros(21)
+    w = np.zeros(7)
+    lib().or_rule7(b, w)
+    return b.reshape(7, 3), w
+
+
+def ss_rule(kase, n):
+    L = lib()
+    cnt = L.or_ss_rule(kase, n, None, None, None)
+    xh = np.zeros(2 * cnt)
+    yh = np.zeros(2 * cnt)
+    w = np.zeros(cnt)
+    L.or_ss_rule(kase, n, xh.ctypes.data, yh.ctypes.data, w.ctypes.data)
+    return xh.reshape(-1, 2), yh.reshape(-1, 2), w
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+class Oracle:
+    """FP64 CPU oracle bound to one mesh and time grid.
+
+    psi_mode: "direct" (1-D Gauss quadrature per evaluation) or "interp"
+    (the oracle's own barycentric interpolant, sampled from the direct mode).
+    """
+
+    def __init__(self, verts, tris, t, p=0, equidistant=True, gl_n=32, gl_sub=4,
+                 ss_n=4, psi_mode="interp", interp_S=8, interp_n=32):
+        self.V = np.ascontiguousarray(verts, dtype=np.float64)
+        self.F = np.ascontiguousarray(tris, dtype=np.int32)
+        self.t = np.ascontiguousarray(t, dtype=np.float64)
+        self.p = p
+        mode = {"direct": 0, "interp": 1}[psi_mode]
+        self.h = lib().or_create(self.V, self.V.shape[0], self.F, self.F.shape[0], self.t, self.t.shape[0],
+                                 p, int(equidistant), gl_n, gl_sub, ss_n, mode, interp_S, interp_n)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_destroy(self.h)
+            self.h = None
+
+    @property
+    def M(self):
+        return self.V.shape[0]
+
+    @property
+    def E(self):
+        return self.F.shape[0]
+
+    @property
+    def N(self):
+        return self.t.shape[0]
+
+    def num_blocks(self):
+        return lib().or_num_blocks(self.h)
+
+    def blocks(self):
+        """list of (kb, ib, m2, m1, a, b): 0-based test/trial time index,
+        temporal orders and the support [a, b] of psi on r >= 0."""
+        out = []
+        for b in range(self.num_blocks()):
+            q = np.zeros(4, np.int32)
+            ab = np.zeros(2)
+            lib().or_block(self.h, b, q, ab)
+            out.append((int(q[0]), int(q[1]), int(q[2]), int(q[3]), float(ab[0]), float(ab[1])))
+        return out
+
+    def diam(self):
+        return lib().or_diam(self.h)
+
+    def tri_geom(self, e):
+        """(unit normal, area, 3x3 surface curls of the corner hat functions)"""
+        out = np.zeros(13)
+        lib().or_tri_geom(self.h, e, out)
+        return out[:3], out[3], out[4:].reshape(3, 3)
+
+    def set_first_kind(self, kind):
+        lib().or_set_first_kind(self.h, kind)
+
+    def basis(self, ib, m, s):
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        out = np.zeros((s.size, 3))
+        lib().or_basis(self.h, ib, m, s, s.size, out)
+        return out
+
+    def mu(self, ib, s):
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        out = np.zeros((s.size, 3))
+        lib().or_mu(self.h, ib, s, s.size, out)
+        return out
+
+    def psi(self, kb, ib, r, m2=0, m1=0):
+        """direct (psi, psi~) of test basis kb against trial basis ib at r"""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        out = np.zeros((r.size, 2))
+        lib().or_psi(self.h, kb, m2, ib, m1, r, r.size, out)
+        return out
+
+    def psi_block(self, blk, r):
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        out = np.zeros((r.size, 2))
+        lib().or_psi_block(self.h, blk, r, r.size, out)
+        return out
+
+    def tri_bounds(self, s, q):
+        out = np.zeros(2)
+        lib().or_tri_bounds(self.h, s, q, out)
+        return out
+
+    def pair_local(self, s, q, blks, far_n=0, near_n=0):
+        blks = np.ascontiguousarray(blks, dtype=np.int64)
+        L = np.zeros(9 * blks.size)
+        lib().or_pair_local(self.h, s, q, blks, blks.size, far_n, near_n, L)
+        return L.reshape(blks.size, 3, 3)
+
+    def assemble_rows(self, rows, blks):
+        """Rows `rows` of blocks `blks`: dict blk -> list over rows of
+        (cols int32, far float64, near float64)."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        blks = np.ascontiguousarray(blks, dtype=np.int64)
+        nr, nb = rows.size, blks.size
+        counts = np.zeros(nr * nb, np.int64)
+        lib().or_pattern_counts(self.h, rows, nr, blks, nb, counts)
+        offs = np.zeros(nr * nb + 1, np.int64)
+        offs[1:] = np.cumsum(counts)
+        tot = int(offs[-1])
+        cols = np.zeros(max(tot, 1), np.int32)
+        vf = np.zeros(max(tot, 1))
+        vn = np.zeros(max(tot, 1))
+        lib().or_assemble_rows(self.h, rows, nr, blks, nb, offs, cols, vf, vn)
+        out = {}
+        for bi, b in enumerate(blks):
+            lst = []
+            for ri in range(nr):
+                a, e = offs[bi * nr + ri], offs[bi * nr + ri + 1]
+                lst.append((cols[a:e].copy(), vf[a:e].copy(), vn[a:e].copy()))
+            out[int(b)] = lst
+        return out
+
+    def dense_block(self, blk):
+        """The whole block as a dense M x M array (far + near), row = test vertex."""
+        res = self.assemble_rows(np.arange(self.M), [blk])[int(blk)]
+        A = np.zeros((self.M, self.M))
+        for l, (c, f, n) in enumerate(res):
+            A[l, c] = f + n
+        return A
