@@ -1,0 +1,181 @@
+/*
+ * tdbem.h -- C ABI of libtdbem, the GB300 (sm_103a) assembler of the
+ * space-time Galerkin system of the time-domain hypersingular operator
+ * (3-D wave equation, Neumann data), after Veit, Merta, Zapletal, Lukas,
+ * "Efficient solution of time-domain boundary integral equations arising in
+ * sound-hard scattering".
+ *
+ * What is assembled (paper Sec. 3, Eq. MatrixEntries):
+ *
+ *   A_{k,i}(l,j) = int_G int_G [ n_x.n_y phi_j(y) phi_l(x) psi_{k,i}(|x-y|)
+ *                   + curl phi_j(y) . curl phi_l(x) psi~_{k,i}(|x-y|) ]
+ *                  / (4 pi |x-y|) dG_y dG_x
+ *
+ *   psi_{k,i}(r) = int_0^T b''_i(t-r) b'_k(t) dt,
+ *   psi~_{k,i}(r) = int_0^T b_i(t-r) b'_k(t) dt          (Eq. psis)
+ *
+ * with continuous piecewise-linear hat functions phi on a flat triangle
+ * mesh and the C-infinity partition-of-unity time basis b of Sec. 3
+ * (Eq. BasisFunctions, p = 0). Row = test (k, l), column = trial (i, j);
+ * every block is spatially symmetric, so this is also the paper's A_{k,i}(j,l).
+ *
+ * Blocks (Sec. 3.2): A is block Hessenberg (Eq. Apartitioned); block (k,i)
+ * vanishes when the support [a,b] of psi_{k,i} (a = max(0, t_{k-2} - t_i),
+ * b = t_k - t_{i-2}, 1-based) starts at or beyond diam(Gamma). On an
+ * equidistant grid only the blocks of Sec. 5.1 are assembled -- the first two
+ * block columns, the last block row, A_{2,3} and A_{N-1,N} -- and every other
+ * block is one of them by Eq. relationAtildeBlock. Within a block, entry
+ * (l,j) is structural iff the open support (a,b) meets [mindist_{l,j},
+ * maxdist_{l,j}] (Eq. SparsitySmallBlock); such entries stay in the pattern
+ * even where they evaluate to 0.
+ *
+ * Quadrature: element pairs without a shared vertex use the 7-point
+ * degree-5 triangle rule on both triangles (49 point pairs); pairs sharing a
+ * vertex, an edge or the triangle use Sauter-Schwab regularising maps with
+ * Gauss-Legendre points per direction. psi and psi~ come from piecewise
+ * Chebyshev tables (Sec. 3.1) built on the device from a direct 1-D
+ * Gauss-Legendre quadrature of Eq. psis.
+ *
+ * Indices are 0-based (the paper's are 1-based): time basis k, i in
+ * 0..N-1 for N grid points t_0 = 0 < ... < t_{N-1} = T.
+ *
+ * Conventions for every call:
+ *   - Host input arrays are copied; the caller keeps ownership.
+ *   - Device pointers returned by tdbem_block_csr are borrowed: valid until
+ *     the next assemble call or tdbem_asm_destroy.
+ *   - Work is queued on the given CUDA stream (cudaStream_t passed as void*,
+ *     NULL = legacy default stream). Calls that return data to the host
+ *     synchronise that stream.
+ *   - Errors are returned as status codes; no exception crosses the ABI and
+ *     nothing aborts. tdbem_last_error() describes the last failure of the
+ *     calling thread.
+ *   - Device memory comes from the allocator registered with
+ *     tdbem_set_allocator (else cudaMalloc / cudaFree).
+ */
+#ifndef TDBEM_H
+#define TDBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tdbem_status;
+#define TDBEM_OK 0
+#define TDBEM_E_INVALID_ARG 1   /* NULL pointer, size or option out of range */
+#define TDBEM_E_MESH 2          /* degenerate triangle, bad index, NaN vertex */
+#define TDBEM_E_TIMEGRID 3      /* N < 3, t_0 != 0, not strictly increasing */
+#define TDBEM_E_OOM 4           /* device allocation failed */
+#define TDBEM_E_CUDA 5          /* a CUDA runtime call failed */
+#define TDBEM_E_DEVICE 6        /* a kernel reported an inconsistency (status word) */
+#define TDBEM_E_NOT_ASSEMBLED 7 /* values requested before an assemble call */
+#define TDBEM_E_UNSUPPORTED 8   /* configuration not supported by this build */
+
+/* Precision of the far field (element pairs without a shared vertex). */
+#define TDBEM_PREC_FP64 0  /* plain: everything in FP64 */
+#define TDBEM_PREC_MIXED 1 /* FP32 quadrature and Chebyshev evaluation with
+                              FP64 element-pair distances; near field FP64 */
+
+/* Which values tdbem_block_csr returns. */
+#define TDBEM_FAR 0  /* full block pattern, values of the element pairs without
+                        a shared vertex: float (MIXED) or double (FP64) */
+#define TDBEM_NEAR 1 /* sub-pattern reached by element pairs sharing a vertex,
+                        their values, double */
+
+typedef struct tdbem_mesh tdbem_mesh;
+typedef struct tdbem_timegrid tdbem_timegrid;
+typedef struct tdbem_asm tdbem_asm;
+
+typedef struct {
+    int32_t precision;     /* TDBEM_PREC_FP64 or TDBEM_PREC_MIXED */
+    int32_t near_order;    /* Gauss-Legendre points per direction, Sauter-Schwab (default 4) */
+    int32_t cheb_degree;   /* Chebyshev degree per panel (32; the only value this build takes) */
+    int32_t reserved[5];
+} tdbem_opts;
+
+typedef struct {
+    int64_t n_blocks;        /* unique blocks assembled */
+    int64_t nnz;             /* stored entries summed over the unique blocks */
+    int64_t nnz_near;        /* entries of the near sub-patterns */
+    int64_t far_pairs;       /* element pairs without a shared vertex */
+    int64_t near_pairs;      /* element pairs sharing a vertex */
+    int64_t quad_points;     /* point pairs x blocks evaluated (far + near) */
+    double ms_total;         /* device time of the last tdbem_assemble_all */
+    double ms_pattern;       /* of which: bounds, windows, table build */
+    double ms_far;           /* far-field quadrature */
+    double ms_near;          /* near-field quadrature */
+    double ms_extract;       /* CSR extraction */
+} tdbem_stats_t;
+
+/* Thread-local description of the last failure; never NULL. */
+const char *tdbem_last_error(void);
+
+/* Register device allocation callbacks (NULL, NULL restores cudaMalloc).
+ * alloc(bytes, stream, ctx) returns a device pointer or NULL;
+ * free_(ptr, stream, ctx) releases it. Applies to objects created later. */
+tdbem_status tdbem_set_allocator(void *(*alloc)(size_t, void *, void *),
+                                 void (*free_)(void *, void *, void *), void *ctx);
+
+/* Surface mesh: M vertices (host, M x 3 doubles, row-major) and E flat
+ * triangles (host, E x 3 int32 vertex indices, counter-clockwise seen from
+ * the side the unit normal points to). Each vertex carries one hat function
+ * phi_j (Sec. 3, "piecewise linear"). Fails with TDBEM_E_MESH on an index out
+ * of range, a repeated index, a zero-area triangle or a non-finite vertex. */
+tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, const int32_t *tris,
+                               int64_t E, tdbem_mesh **out);
+
+/* Time grid of N points (host): t[0] = 0 < t[1] < ... < t[N-1] = T (Sec. 3).
+ * p: Legendre degree of the time basis (only 0 in this build); basis_kind: 0
+ * = the paper's step f = erf(2 artanh x)/2 + 1/2; c: wave speed (> 0, r =
+ * |x-y|/c). An equidistant grid (|t_i - i T/(N-1)| <= 1e-12 T) uses the
+ * Toeplitz block reuse of Sec. 5.1 and needs N >= 5; other grids are not
+ * supported by this build (TDBEM_E_UNSUPPORTED). */
+tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t basis_kind,
+                                   double c, tdbem_timegrid **out);
+
+/* Plan an assembler on the current CUDA device: the unique block list, the
+ * device copies of the geometry and the triangle colouring. opts may be
+ * NULL (defaults: MIXED, near_order 4, degree 32). */
+tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid *tg,
+                                    const tdbem_opts *opts, void *stream, tdbem_asm **out);
+
+/* Number of unique blocks, and block b's test / trial time index (0-based),
+ * temporal orders and structural entry counts (after an assemble call;
+ * -1 before). */
+tdbem_status tdbem_num_blocks(const tdbem_asm *a, int64_t *n_unique);
+tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t *i,
+                              int32_t *m2, int32_t *m1, int64_t *nnz_far, int64_t *nnz_near);
+
+/* Assemble every unique block: psi tables, element-pair bounds, vertex-pair
+ * windows, far and near quadrature, CSR extraction. Synchronises the stream
+ * at the end and returns TDBEM_E_DEVICE if a kernel flagged an inconsistency. */
+tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
+
+/* CSR of unique block b (borrowed device pointers). which = TDBEM_FAR: M+1
+ * int64 row offsets, int32 sorted columns and float (MIXED) / double (FP64)
+ * values; TDBEM_NEAR: the near sub-pattern with double values. Any output
+ * pointer may be NULL. */
+tdbem_status tdbem_block_csr(const tdbem_asm *a, int64_t b, int32_t which,
+                             const int64_t **row_ptr_dev, const int32_t **col_dev,
+                             const void **val_dev, int64_t *nnz);
+
+/* Copy of block b's CSR into caller-owned host buffers: rp (M+1 int64), col
+ * (nnz int32) and val (nnz float for TDBEM_FAR in MIXED mode, else double),
+ * sizes as reported by tdbem_block_csr / tdbem_block_info. Any buffer may be
+ * NULL. Synchronous (device-wide cudaMemcpy). */
+tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32_t which, int64_t *rp,
+                                  int32_t *col, void *val);
+
+/* Assembly counters and the per-phase device times of the last assembly. */
+tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
+
+void tdbem_mesh_destroy(tdbem_mesh *m);
+void tdbem_timegrid_destroy(tdbem_timegrid *t);
+void tdbem_asm_destroy(tdbem_asm *a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDBEM_H */

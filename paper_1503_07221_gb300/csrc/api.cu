@@ -1,0 +1,913 @@
+// Host side of libtdbem: the C ABI declared in include/tdbem.h, input
+// validation, the planner (unique blocks, block classes, colouring, chunk
+// plans, neighbour lists, quadrature rules) and the launch sequence of one
+// assembly.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "tdbem_internal.h"
+
+using namespace tdbem;
+
+// ------------------------------------------------------------ error state
+static thread_local std::string g_err = "no error";
+
+static tdbem_status fail(tdbem_status code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(TDBEM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// --------------------------------------------------------------- allocator
+static void *(*g_alloc)(size_t, void *, void *) = nullptr;
+static void (*g_free)(void *, void *, void *) = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    void *(*alloc)(size_t, void *, void *) = nullptr;
+    void (*free_)(void *, void *, void *) = nullptr;
+    void *ctx = nullptr;
+    cudaStream_t st = nullptr;
+    void release() {
+        if (!p) return;
+        if (free_) free_(p, st, ctx);
+        else cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+};
+
+static tdbem_status dev_alloc(DevBuf &b, size_t bytes, cudaStream_t st) {
+    b.release();
+    if (bytes == 0) bytes = 16;
+    b.alloc = g_alloc; b.free_ = g_free; b.ctx = g_alloc_ctx; b.st = st;
+    if (g_alloc) b.p = g_alloc(bytes, st, g_alloc_ctx);
+    else if (cudaMalloc(&b.p, bytes) != cudaSuccess) b.p = nullptr;
+    if (!b.p) {
+        cudaGetLastError();
+        return fail(TDBEM_E_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    b.n = bytes;
+    return TDBEM_OK;
+}
+
+template <typename T>
+static tdbem_status upload(DevBuf &b, const std::vector<T> &v, cudaStream_t st) {
+    tdbem_status s = dev_alloc(b, v.size() * sizeof(T), st);
+    if (s) return s;
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return TDBEM_OK;
+}
+
+// ------------------------------------------------------- quadrature rules
+// Gauss-Legendre nodes and weights on [0,1] (Newton on P_n from the
+// Chebyshev-like initial guess cos(pi (i + 3/4)/(n + 1/2))).
+static void gauss_legendre01(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            if (n == 1) { p0 = 1.0; p1 = z; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) { const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[n - 1 - i] = 0.5 * (z + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Radon's 7-point rule of degree 5 on a triangle: barycentric points and
+// weights summing to 1 (centroid, and two 3-point orbits built from sqrt(15)).
+static void radon7(double L[7][3], double W[7]) {
+    const double s = sqrt(15.0);
+    const double a1 = (6.0 - s) / 21.0, b1 = 1.0 - 2.0 * a1, w1 = (155.0 - s) / 1200.0;
+    const double a2 = (6.0 + s) / 21.0, b2 = 1.0 - 2.0 * a2, w2 = (155.0 + s) / 1200.0;
+    const double P[7][3] = {{1.0 / 3, 1.0 / 3, 1.0 / 3}, {b1, a1, a1}, {a1, b1, a1}, {a1, a1, b1},
+                            {b2, a2, a2}, {a2, b2, a2}, {a2, a2, b2}};
+    for (int k = 0; k < 7; ++k) {
+        for (int d = 0; d < 3; ++d) L[k][d] = P[k][d];
+        W[k] = k == 0 ? 9.0 / 40.0 : (k < 4 ? w1 : w2);
+    }
+}
+
+// Sauter-Schwab rule on T x T with T = {0 <= x2 <= x1 <= 1} (area 1/2):
+// the regularising substitutions for identical triangles (6 regions, weight
+// xi^3 e1^2 e2), a common edge from (0,0) to (1,0) (5 regions, weights
+// xi^3 e1^2 and xi^3 e1^2 e2) and a common vertex (0,0) (2 regions, weight
+// xi^3 e2), tensor Gauss-Legendre with n points per direction on [0,1]^4.
+// Output rows: x1, x2, y1, y2, weight.
+static std::vector<double> sauter_schwab(int kase, int n) {
+    std::vector<double> gx, gw;
+    gauss_legendre01(n, gx, gw);
+    std::vector<double> out;
+    for (int i0 = 0; i0 < n; ++i0)
+        for (int i1 = 0; i1 < n; ++i1)
+            for (int i2 = 0; i2 < n; ++i2)
+                for (int i3 = 0; i3 < n; ++i3) {
+                    const double xi = gx[i0], a = gx[i1], b = gx[i2], c = gx[i3];
+                    const double W = gw[i0] * gw[i1] * gw[i2] * gw[i3];
+                    auto put = [&](double x1, double x2, double y1, double y2, double j) {
+                        out.push_back(x1); out.push_back(x2); out.push_back(y1); out.push_back(y2);
+                        out.push_back(W * j);
+                    };
+                    if (kase == 3) {
+                        const double j = xi * xi * xi * a * a * b;
+                        const double u1 = xi, u2 = xi * (1 - a + a * b), v1 = xi * (1 - a * b * c), v2 = xi * (1 - a);
+                        put(u1, u2, v1, v2, j); put(v1, v2, u1, u2, j);
+                        const double p1 = xi, p2 = xi * a * (1 - b + b * c), q1 = xi * (1 - a * b), q2 = xi * a * (1 - b);
+                        put(p1, p2, q1, q2, j); put(q1, q2, p1, p2, j);
+                        const double r1 = xi * (1 - a * b * c), r2 = xi * a * (1 - b * c), s1 = xi, s2 = xi * a * (1 - b);
+                        put(r1, r2, s1, s2, j); put(s1, s2, r1, r2, j);
+                    } else if (kase == 2) {
+                        const double j0 = xi * xi * xi * a * a, j1 = j0 * b;
+                        put(xi, xi * a * c, xi * (1 - a * b), xi * a * (1 - b), j0);
+                        put(xi, xi * a, xi * (1 - a * b * c), xi * a * b * (1 - c), j1);
+                        put(xi * (1 - a * b), xi * a * (1 - b), xi, xi * a * b * c, j1);
+                        put(xi * (1 - a * b * c), xi * a * b * (1 - c), xi, xi * a, j1);
+                        put(xi * (1 - a * b * c), xi * a * (1 - b * c), xi, xi * a * b, j1);
+                    } else {
+                        const double j = xi * xi * xi * b;
+                        put(xi, xi * a, xi * b, xi * b * c, j);
+                        put(xi * b, xi * b * c, xi, xi * a, j);
+                    }
+                }
+    return out;
+}
+
+// ------------------------------------------------------------------- mesh
+struct tdbem_mesh {
+    int64_t M = 0, E = 0;
+    std::vector<double> V;
+    std::vector<int32_t> F;
+    std::vector<double> cen, dq, geo64;
+    std::vector<float> dq32, geo32;
+    std::vector<int64_t> vt_ptr;
+    std::vector<int32_t> vt_tri;
+    std::vector<int64_t> adj_ptr;
+    std::vector<int32_t> adj_tri;
+    std::vector<int8_t> adj_perm;
+    std::vector<int32_t> adj_nbr;
+    std::vector<int64_t> nbr_ptr;
+    std::vector<int32_t> nbr;
+    int NB = 0;
+    std::vector<std::vector<int32_t>> colors;
+    std::vector<int32_t> chunk_vptr, chunk_vert, chunk_sptr, chunk_src;
+    int64_t nchunks = 0;
+    double diam = 0.0, max_dq = 0.0, max_star = 0.0;
+    double rule_L[7][3], rule_W[7];
+};
+
+static tdbem_status build_mesh(tdbem_mesh &m) {
+    const int64_t M = m.M, E = m.E;
+    const double *V = m.V.data();
+    const int32_t *F = m.F.data();
+    radon7(m.rule_L, m.rule_W);
+    m.cen.assign(3 * E, 0.0);
+    m.dq.assign(21 * E, 0.0);
+    m.dq32.assign(21 * E, 0.f);
+    m.geo64.assign(16 * E, 0.0);
+    m.geo32.assign(16 * E, 0.f);
+    for (int64_t e = 0; e < E; ++e) {
+        const double *P[3] = {V + 3 * F[3 * e], V + 3 * F[3 * e + 1], V + 3 * F[3 * e + 2]};
+        double u[3], v[3], c[3];
+        for (int d = 0; d < 3; ++d) { u[d] = P[1][d] - P[0][d]; v[d] = P[2][d] - P[0][d]; }
+        c[0] = u[1] * v[2] - u[2] * v[1];
+        c[1] = u[2] * v[0] - u[0] * v[2];
+        c[2] = u[0] * v[1] - u[1] * v[0];
+        const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (!(len > 0.0) || !std::isfinite(len))
+            return fail(TDBEM_E_MESH, "triangle " + std::to_string(e) + " has zero area");
+        const double area = 0.5 * len;
+        double *g = m.geo64.data() + 16 * e;
+        for (int d = 0; d < 3; ++d) g[d] = c[d] / len;
+        g[3] = area;
+        // surface curl of the hat function of corner a: n x grad lambda_a = -(P_{a+2} - P_{a+1}) / (2|T|)
+        for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d) g[4 + 3 * a + d] = -(P[(a + 2) % 3][d] - P[(a + 1) % 3][d]) / (2.0 * area);
+        for (int k = 0; k < 16; ++k) m.geo32[16 * e + k] = (float)g[k];
+        for (int d = 0; d < 3; ++d) m.cen[3 * e + d] = (P[0][d] + P[1][d] + P[2][d]) / 3.0;
+        for (int k = 0; k < 7; ++k)
+            for (int d = 0; d < 3; ++d) {
+                const double x = m.rule_L[k][0] * P[0][d] + m.rule_L[k][1] * P[1][d] + m.rule_L[k][2] * P[2][d];
+                m.dq[21 * e + 3 * k + d] = x - m.cen[3 * e + d];
+                m.dq32[21 * e + 3 * k + d] = (float)m.dq[21 * e + 3 * k + d];
+            }
+        for (int k = 0; k < 7; ++k) {
+            const double *q = m.dq.data() + 21 * e + 3 * k;
+            m.max_dq = std::max(m.max_dq, sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]));
+        }
+    }
+    // vertex -> triangles
+    m.vt_ptr.assign(M + 1, 0);
+    for (int64_t e = 0; e < E; ++e)
+        for (int a = 0; a < 3; ++a) m.vt_ptr[F[3 * e + a] + 1]++;
+    for (int64_t v = 0; v < M; ++v) m.vt_ptr[v + 1] += m.vt_ptr[v];
+    m.vt_tri.assign(3 * E, 0);
+    {
+        std::vector<int64_t> fill(m.vt_ptr.begin(), m.vt_ptr.end() - 1);
+        for (int64_t e = 0; e < E; ++e)
+            for (int a = 0; a < 3; ++a) m.vt_tri[fill[F[3 * e + a]]++] = (int32_t)e;
+    }
+    for (int64_t v = 0; v < M; ++v)
+        if (m.vt_ptr[v + 1] == m.vt_ptr[v]) return fail(TDBEM_E_MESH, "vertex " + std::to_string(v) + " belongs to no triangle");
+    // triangles sharing a vertex with tau (tau included), with the corner
+    // permutations that put the shared vertices first in the same order
+    m.adj_ptr.assign(E + 1, 0);
+    m.adj_tri.clear();
+    m.adj_perm.clear();
+    for (int64_t t = 0; t < E; ++t) {
+        std::set<int32_t> s;
+        for (int a = 0; a < 3; ++a)
+            for (int64_t x = m.vt_ptr[F[3 * t + a]]; x < m.vt_ptr[F[3 * t + a] + 1]; ++x) s.insert(m.vt_tri[x]);
+        for (int32_t q : s) {
+            int pa[3] = {0, 1, 2}, pb[3] = {0, 1, 2};
+            int shared = 0, ia[3], ib[3];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    if (F[3 * t + a] == F[3 * q + b]) { ia[shared] = a; ib[shared] = b; ++shared; }
+            if (shared == 2) {
+                pa[0] = ia[0]; pa[1] = ia[1]; pa[2] = 3 - ia[0] - ia[1];
+                pb[0] = ib[0]; pb[1] = ib[1]; pb[2] = 3 - ib[0] - ib[1];
+            } else if (shared == 1) {
+                for (int k = 0; k < 3; ++k) { pa[k] = (ia[0] + k) % 3; pb[k] = (ib[0] + k) % 3; }
+            } else if (shared == 3) {
+                if (q != t) return fail(TDBEM_E_MESH, "triangles " + std::to_string(t) + " and " + std::to_string(q) + " repeat the same vertices");
+            }
+            m.adj_tri.push_back(q);
+            const int8_t rec[8] = {(int8_t)shared, (int8_t)pa[0], (int8_t)pa[1], (int8_t)pa[2],
+                                   (int8_t)pb[0], (int8_t)pb[1], (int8_t)pb[2], 0};
+            m.adj_perm.insert(m.adj_perm.end(), rec, rec + 8);
+        }
+        m.adj_ptr[t + 1] = (int64_t)m.adj_tri.size();
+    }
+    // near neighbour lists: j reached from l by an adjacent element pair
+    std::vector<std::vector<int32_t>> nb(M);
+    for (int64_t t = 0; t < E; ++t)
+        for (int64_t x = m.adj_ptr[t]; x < m.adj_ptr[t + 1]; ++x)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) nb[F[3 * t + a]].push_back(F[3 * m.adj_tri[x] + b]);
+    m.nbr_ptr.assign(M + 1, 0);
+    m.nbr.clear();
+    m.NB = 0;
+    for (int64_t v = 0; v < M; ++v) {
+        std::sort(nb[v].begin(), nb[v].end());
+        nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+        m.nbr.insert(m.nbr.end(), nb[v].begin(), nb[v].end());
+        m.nbr_ptr[v + 1] = (int64_t)m.nbr.size();
+        m.NB = std::max(m.NB, (int)nb[v].size());
+    }
+    m.adj_nbr.assign(9 * m.adj_tri.size(), -1);
+    for (int64_t t = 0; t < E; ++t)
+        for (int64_t x = m.adj_ptr[t]; x < m.adj_ptr[t + 1]; ++x) {
+            const int8_t *pm = m.adj_perm.data() + 8 * x;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const int32_t l = F[3 * t + pm[1 + a]], j = F[3 * m.adj_tri[x] + pm[4 + b]];
+                    const auto &L = nb[l];
+                    m.adj_nbr[9 * x + 3 * a + b] = (int32_t)(std::lower_bound(L.begin(), L.end(), j) - L.begin());
+                }
+        }
+    // greedy colouring: no two triangles of one colour share a vertex
+    std::vector<int> col(E, -1);
+    int ncol = 0;
+    for (int64_t t = 0; t < E; ++t) {
+        std::vector<char> used(64, 0);
+        for (int64_t x = m.adj_ptr[t]; x < m.adj_ptr[t + 1]; ++x) {
+            const int c = col[m.adj_tri[x]];
+            if (c >= 0 && c < 64) used[c] = 1;
+        }
+        int c = 0;
+        while (c < 64 && used[c]) ++c;
+        if (c == 64) return fail(TDBEM_E_MESH, "vertex valence too high for the colouring");
+        col[t] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    m.colors.assign(ncol, {});
+    for (int64_t t = 0; t < E; ++t) m.colors[col[t]].push_back((int32_t)t);
+    // chunk plans: for 32 consecutive trial triangles, their vertices and
+    // the (triangle, corner) sources of each vertex
+    m.nchunks = (E + 31) / 32;
+    m.chunk_vptr.assign(m.nchunks + 1, 0);
+    m.chunk_vert.clear();
+    m.chunk_sptr.clear();
+    m.chunk_src.clear();
+    for (int64_t ch = 0; ch < m.nchunks; ++ch) {
+        std::map<int32_t, std::vector<int32_t>> vs;
+        for (int s = 0; s < 32 && ch * 32 + s < E; ++s)
+            for (int b = 0; b < 3; ++b) vs[F[3 * (ch * 32 + s) + b]].push_back(3 * s + b);
+        for (auto &kv : vs) {
+            m.chunk_vert.push_back(kv.first);
+            m.chunk_sptr.push_back((int32_t)m.chunk_src.size());
+            m.chunk_src.insert(m.chunk_src.end(), kv.second.begin(), kv.second.end());
+        }
+        m.chunk_vptr[ch + 1] = (int32_t)m.chunk_vert.size();
+    }
+    m.chunk_sptr.push_back((int32_t)m.chunk_src.size());
+    // diameter (largest vertex distance) and largest star diameter
+    double dm = 0.0;
+    for (int64_t i = 0; i < M; ++i)
+        for (int64_t j = i + 1; j < M; ++j) {
+            const double a = V[3 * i] - V[3 * j], b = V[3 * i + 1] - V[3 * j + 1], c = V[3 * i + 2] - V[3 * j + 2];
+            const double v = a * a + b * b + c * c;
+            if (v > dm) dm = v;
+        }
+    m.diam = sqrt(dm);
+    for (int64_t v = 0; v < M; ++v) {
+        std::vector<int32_t> pts;
+        for (int64_t x = m.vt_ptr[v]; x < m.vt_ptr[v + 1]; ++x)
+            for (int a = 0; a < 3; ++a) pts.push_back(F[3 * m.vt_tri[x] + a]);
+        for (size_t i = 0; i < pts.size(); ++i)
+            for (size_t j = i + 1; j < pts.size(); ++j) {
+                const double *p = V + 3 * pts[i], *q = V + 3 * pts[j];
+                const double d = sqrt((p[0] - q[0]) * (p[0] - q[0]) + (p[1] - q[1]) * (p[1] - q[1]) + (p[2] - q[2]) * (p[2] - q[2]));
+                m.max_star = std::max(m.max_star, d);
+            }
+    }
+    return TDBEM_OK;
+}
+
+// --------------------------------------------------------------- time grid
+struct tdbem_timegrid {
+    int64_t N = 0;
+    int p = 0, kind = 0;
+    double c = 1.0, T = 0.0, dt = 0.0;
+    bool equidistant = false;
+    std::vector<double> t;
+};
+
+// -------------------------------------------------------------- assembler
+struct Block {
+    int kb, ib, cls, lag;
+    double a, b;
+};
+
+struct tdbem_asm {
+    const tdbem_mesh *mesh = nullptr;
+    const tdbem_timegrid *tg = nullptr;
+    tdbem_opts opts{};
+    bool fp64 = false;
+    int OFF = 1, KW = 8, S64 = 4;
+    std::vector<Block> blocks;
+    int cls_dlo[NCLASS], cls_dhi[NCLASS], cls_rho[NCLASS], cls_P[NCLASS];
+    std::vector<int> blk_of_lag, lag_base, blk_of_spec;
+    std::vector<std::vector<double>> lag_a, lag_b;
+    // device buffers
+    DevBuf F, V, cen, dq, dq32, geo32, geo64, vt_ptr, vt_tri, adj_ptr, adj_tri, adj_perm, adj_nbr,
+        nbr_ptr, nbr, chunk_vptr, chunk_vert, chunk_sptr, chunk_src, colors, rule_w, rule_l, tgrid,
+        lagA, lagB, rec, wdlo, wdhi, wsmask, dense, dense_spec, ndense, ndense_spec, status,
+        cls_dlo_d, cls_dhi_d, blk_of_lag_d, lag_base_d, blk_of_spec_d, cnt_far, cnt_near, rp_far,
+        rp_near, tot_far, tot_near, off_far_d, off_near_d, col_far, val_far, col_near, val_near,
+        tab_kb, tab_ib, tab_r0, tab_samples, tab_coef1, tab_coef4, gl_x, gl_w, ss[4], quad_partial;
+    std::vector<int64_t> color_off;
+    int ss_npp[4] = {0, 0, 0, 0};
+    ChebF32 c32{};
+    std::vector<int64_t> nnz_far, nnz_near, off_far, off_near;
+    bool assembled = false;
+    tdbem_stats_t stats{};
+    size_t col_far_cap = 0, col_near_cap = 0;
+};
+
+static int kind_of(int64_t i, int64_t N) { return i == 0 ? 0 : (i == N - 1 ? 2 : 1); }  // F, I, L
+
+static tdbem_status plan_blocks(tdbem_asm &A) {
+    const tdbem_timegrid &tg = *A.tg;
+    const int64_t N = tg.N;
+    const double *t = tg.t.data();
+    const double T = t[N - 1];
+    auto tl = [&](int64_t q) { return q == 0 ? 0.0 : t[q - 1]; };
+    auto tr = [&](int64_t q) { return q == N - 1 ? T : t[q + 1]; };
+    A.blocks.clear();
+    for (int c = 0; c < NCLASS; ++c) { A.cls_dlo[c] = 1 << 20; A.cls_dhi[c] = -(1 << 20); }
+    for (int64_t k = 0; k < N; ++k)
+        for (int64_t i = 0; i < N; ++i) {
+            const bool want = i == 0 || i == 1 || k == N - 1 || (k == 1 && i == 2) || (k == N - 2 && i == N - 1);
+            if (!want || i > k + 1) continue;
+            const double a = std::max(0.0, tl(k) - tr(i)), b = tr(k) - tl(i);
+            if (!(b > a) || a >= A.mesh->diam) continue;
+            const int kk = kind_of(k, N), ki = kind_of(i, N);
+            int cls, lag;
+            if (kk == 1 && ki == 0) { cls = C1; lag = (int)k; }
+            else if (kk == 1 && ki == 1) { cls = C2; lag = (int)(k - i); }
+            else if (kk == 2 && ki == 1) { cls = C3; lag = (int)(N - 1 - i); }
+            else if (kk == 0 && ki == 0) { cls = S00; lag = 0; }
+            else if (kk == 0 && ki == 1) { cls = S01; lag = 0; }
+            else if (kk == 2 && ki == 0) { cls = SN0; lag = 0; }
+            else if (kk == 2 && ki == 2) { cls = SNN; lag = 0; }
+            else if (kk == 1 && ki == 2) { cls = SN1N; lag = 0; }
+            else return fail(TDBEM_E_UNSUPPORTED, "unexpected block kind");
+            A.blocks.push_back({(int)k, (int)i, cls, lag, a, b});
+            A.cls_dlo[cls] = std::min(A.cls_dlo[cls], lag);
+            A.cls_dhi[cls] = std::max(A.cls_dhi[cls], lag);
+        }
+    // lag tables and block lookup
+    A.lag_a.assign(NCLASS, {});
+    A.lag_b.assign(NCLASS, {});
+    A.lag_base.assign(NLAG + 1, 0);
+    A.blk_of_spec.assign(NSPEC, -1);
+    for (int c = 0; c < NLAG; ++c) {
+        const int n = A.cls_dhi[c] >= A.cls_dlo[c] ? A.cls_dhi[c] - A.cls_dlo[c] + 1 : 0;
+        A.lag_base[c + 1] = A.lag_base[c] + n;
+        A.lag_a[c].assign(n, NAN);
+        A.lag_b[c].assign(n, NAN);
+    }
+    A.blk_of_lag.assign(std::max(1, A.lag_base[NLAG]), -1);
+    for (size_t bi = 0; bi < A.blocks.size(); ++bi) {
+        const Block &b = A.blocks[bi];
+        if (b.cls < NLAG) {
+            const int x = b.lag - A.cls_dlo[b.cls];
+            A.lag_a[b.cls][x] = b.a;
+            A.lag_b[b.cls][x] = b.b;
+            A.blk_of_lag[A.lag_base[b.cls] + x] = (int)bi;
+        } else {
+            A.lag_a[b.cls] = {b.a};
+            A.lag_b[b.cls] = {b.b};
+            A.blk_of_spec[b.cls - NLAG] = (int)bi;
+        }
+    }
+    for (int c = 0; c < NLAG; ++c)
+        for (size_t x = 0; x < A.lag_a[c].size(); ++x)
+            if (std::isnan(A.lag_a[c][x])) return fail(TDBEM_E_UNSUPPORTED, "non-contiguous lag range");
+    // panels of each class: rho in units of dt, P panels
+    const double dt = tg.dt;
+    const int Pc[NCLASS] = {3, 4, 3, 1, 1, 2, 1, 1};
+    for (int c = 0; c < NCLASS; ++c) {
+        A.cls_P[c] = Pc[c];
+        A.cls_rho[c] = c < NLAG ? -2 : (c == SN0 ? (int)(N - 3) : 0);
+    }
+    (void)dt;
+    return TDBEM_OK;
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+const char *tdbem_last_error(void) { return g_err.c_str(); }
+
+tdbem_status tdbem_set_allocator(void *(*alloc)(size_t, void *, void *), void (*free_)(void *, void *, void *),
+                                 void *ctx) {
+    if ((alloc == nullptr) != (free_ == nullptr)) return fail(TDBEM_E_INVALID_ARG, "alloc and free must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = free_;
+    g_alloc_ctx = ctx;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_mesh_create(const double *verts, int64_t M, const int32_t *tris, int64_t E, tdbem_mesh **out) {
+    if (!out) return fail(TDBEM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!verts || !tris || M < 3 || E < 1) return fail(TDBEM_E_INVALID_ARG, "need M >= 3 vertices and E >= 1 triangles");
+    if (M > 65535 || E > 65535) return fail(TDBEM_E_UNSUPPORTED, "this build takes M <= 65535 and E <= 65535");
+    for (int64_t i = 0; i < 3 * M; ++i)
+        if (!std::isfinite(verts[i])) return fail(TDBEM_E_MESH, "non-finite vertex coordinate");
+    for (int64_t e = 0; e < E; ++e) {
+        for (int a = 0; a < 3; ++a)
+            if (tris[3 * e + a] < 0 || tris[3 * e + a] >= M) return fail(TDBEM_E_MESH, "triangle " + std::to_string(e) + " has a vertex index out of range");
+        if (tris[3 * e] == tris[3 * e + 1] || tris[3 * e] == tris[3 * e + 2] || tris[3 * e + 1] == tris[3 * e + 2])
+            return fail(TDBEM_E_MESH, "triangle " + std::to_string(e) + " repeats a vertex");
+    }
+    tdbem_mesh *m = new tdbem_mesh();
+    m->M = M;
+    m->E = E;
+    m->V.assign(verts, verts + 3 * M);
+    m->F.assign(tris, tris + 3 * E);
+    tdbem_status s = build_mesh(*m);
+    if (s) { delete m; return s; }
+    *out = m;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t kind, double c, tdbem_timegrid **out) {
+    if (!out) return fail(TDBEM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!t) return fail(TDBEM_E_INVALID_ARG, "t is NULL");
+    if (N < 3) return fail(TDBEM_E_TIMEGRID, "need N >= 3 grid points");
+    if (t[0] != 0.0) return fail(TDBEM_E_TIMEGRID, "t[0] must be 0");
+    for (int64_t i = 1; i < N; ++i)
+        if (!(t[i] > t[i - 1]) || !std::isfinite(t[i])) return fail(TDBEM_E_TIMEGRID, "t must be finite and strictly increasing");
+    if (p != 0) return fail(TDBEM_E_UNSUPPORTED, "this build takes temporal degree p = 0");
+    if (kind != 0) return fail(TDBEM_E_UNSUPPORTED, "this build takes basis_kind 0 (erf(2 artanh))");
+    if (!(c > 0.0) || !std::isfinite(c)) return fail(TDBEM_E_INVALID_ARG, "wave speed must be positive");
+    tdbem_timegrid *g = new tdbem_timegrid();
+    g->N = N;
+    g->p = p;
+    g->kind = kind;
+    g->c = c;
+    // r = |x - y| / c: scale time by c so the kernels work with c = 1
+    g->t.resize(N);
+    for (int64_t i = 0; i < N; ++i) g->t[i] = t[i] * c;
+    g->T = g->t[N - 1];
+    g->dt = g->T / (double)(N - 1);
+    g->equidistant = true;
+    for (int64_t i = 0; i < N; ++i)
+        if (fabs(g->t[i] - i * g->dt) > 1e-12 * g->T) g->equidistant = false;
+    *out = g;
+    return TDBEM_OK;
+}
+
+void tdbem_mesh_destroy(tdbem_mesh *m) { delete m; }
+void tdbem_timegrid_destroy(tdbem_timegrid *t) { delete t; }
+void tdbem_asm_destroy(tdbem_asm *a) { delete a; }
+
+tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid *tg, const tdbem_opts *opts,
+                                    void *stream, tdbem_asm **out) {
+    if (!out || !mesh || !tg) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!tg->equidistant) return fail(TDBEM_E_UNSUPPORTED, "this build assembles equidistant time grids only");
+    if (tg->N < 5 || tg->N > 1000) return fail(TDBEM_E_UNSUPPORTED, "need 5 <= N <= 1000 grid points");
+    if (tg->c != 1.0 && tg->c <= 0.0) return fail(TDBEM_E_INVALID_ARG, "bad wave speed");
+    tdbem_opts o{};
+    o.precision = TDBEM_PREC_MIXED;
+    o.near_order = 4;
+    o.cheb_degree = 32;
+    if (opts) o = *opts;
+    if (o.precision != TDBEM_PREC_FP64 && o.precision != TDBEM_PREC_MIXED) return fail(TDBEM_E_INVALID_ARG, "precision");
+    if (o.near_order < 1 || o.near_order > 5) return fail(TDBEM_E_INVALID_ARG, "near_order must be in 1..5");
+    if (o.cheb_degree != 32) return fail(TDBEM_E_UNSUPPORTED, "cheb_degree must be 32");
+    cudaStream_t st = (cudaStream_t)stream;
+    tdbem_asm *A = new tdbem_asm();
+    A->mesh = mesh;
+    A->tg = tg;
+    A->opts = o;
+    A->fp64 = o.precision == TDBEM_PREC_FP64;
+    auto bail = [&](tdbem_status s) { delete A; return s; };
+    tdbem_status s = plan_blocks(*A);
+    if (s) return bail(s);
+    const double dt = tg->dt;
+    const double spread = 2.0 * mesh->max_dq / dt;
+    A->OFF = (int)ceil(spread + 1e-9);
+    if (A->OFF < 1) A->OFF = 1;
+    if (A->OFF > 3) return bail(fail(TDBEM_E_UNSUPPORTED, "triangles too large for the time step (2 max|x - c|/dt > 3)"));
+    A->KW = 4 + (int)ceil(2.0 * mesh->max_star / dt) + 2;
+    const tdbem_mesh &m = *mesh;
+    // uploads
+    std::vector<int32_t> colors;
+    A->color_off.assign(1, 0);
+    for (auto &c : m.colors) { colors.insert(colors.end(), c.begin(), c.end()); A->color_off.push_back((int64_t)colors.size()); }
+    std::vector<float> rw(7), rl(21);
+    for (int k = 0; k < 7; ++k) { rw[k] = (float)m.rule_W[k]; for (int d = 0; d < 3; ++d) rl[3 * k + d] = (float)m.rule_L[k][d]; }
+#define UP(buf, vec) if ((s = upload(A->buf, vec, st))) return bail(s)
+    UP(F, m.F); UP(V, m.V); UP(cen, m.cen); UP(dq, m.dq); UP(dq32, m.dq32); UP(geo32, m.geo32); UP(geo64, m.geo64);
+    UP(vt_ptr, m.vt_ptr); UP(vt_tri, m.vt_tri); UP(adj_ptr, m.adj_ptr); UP(adj_tri, m.adj_tri);
+    UP(adj_perm, m.adj_perm); UP(adj_nbr, m.adj_nbr); UP(nbr_ptr, m.nbr_ptr); UP(nbr, m.nbr);
+    UP(chunk_vptr, m.chunk_vptr); UP(chunk_vert, m.chunk_vert); UP(chunk_sptr, m.chunk_sptr);
+    UP(chunk_src, m.chunk_src); UP(colors, colors); UP(rule_w, rw); UP(rule_l, rl); UP(tgrid, tg->t);
+    std::vector<double> la, lb;
+    std::vector<int> loff(NCLASS + 1, 0);
+    for (int c = 0; c < NCLASS; ++c) {
+        la.insert(la.end(), A->lag_a[c].begin(), A->lag_a[c].end());
+        lb.insert(lb.end(), A->lag_b[c].begin(), A->lag_b[c].end());
+        loff[c + 1] = (int)la.size();
+    }
+    UP(lagA, la); UP(lagB, lb);
+    std::vector<int> cdlo(A->cls_dlo, A->cls_dlo + NCLASS), cdhi(A->cls_dhi, A->cls_dhi + NCLASS);
+    UP(cls_dlo_d, cdlo); UP(cls_dhi_d, cdhi); UP(blk_of_lag_d, A->blk_of_lag); UP(lag_base_d, A->lag_base);
+    UP(blk_of_spec_d, A->blk_of_spec);
+    // psi table jobs: every panel of every class at 1 (FP32) and S64 (FP64) sub-panels
+    {
+        std::vector<int> kb, ib;
+        std::vector<double> r0;
+        const int64_t N = tg->N;
+        for (int S : {1, A->S64}) {
+            for (int c = 0; c < NCLASS; ++c) {
+                int rk, ri, dr;
+                switch (c) {
+                    case C1: rk = 2; ri = 0; dr = 2; break;
+                    case C2: rk = 3; ri = 1; dr = 2; break;
+                    case C3: rk = (int)N - 1; ri = (int)N - 3; dr = 2; break;
+                    case S00: rk = 0; ri = 0; dr = 0; break;
+                    case S01: rk = 0; ri = 1; dr = 0; break;
+                    case SN0: rk = (int)N - 1; ri = 0; dr = 0; break;
+                    case SNN: rk = (int)N - 1; ri = (int)N - 1; dr = 0; break;
+                    default: rk = (int)N - 2; ri = (int)N - 1; dr = 0; break;
+                }
+                for (int j = 0; j < A->cls_P[c]; ++j)
+                    for (int sb = 0; sb < S; ++sb) {
+                        kb.push_back(rk);
+                        ib.push_back(ri);
+                        r0.push_back((dr + A->cls_rho[c] + j + (double)sb / S) * dt);
+                    }
+            }
+        }
+        UP(tab_kb, kb); UP(tab_ib, ib); UP(tab_r0, r0);
+        std::vector<double> gx, gw;
+        gauss_legendre01(24, gx, gw);
+        UP(gl_x, gx); UP(gl_w, gw);
+        if ((s = dev_alloc(A->tab_samples, kb.size() * NCHEB * 2 * sizeof(double), st))) return bail(s);
+        if ((s = dev_alloc(A->tab_coef1, TOTAL_PANELS * NCHEB * 2 * sizeof(double), st))) return bail(s);
+        if ((s = dev_alloc(A->tab_coef4, (size_t)TOTAL_PANELS * A->S64 * NCHEB * 2 * sizeof(double), st))) return bail(s);
+    }
+    for (int k = 1; k <= 3; ++k) {
+        std::vector<double> r = sauter_schwab(k, o.near_order);
+        A->ss_npp[k] = (int)(r.size() / 5);
+        UP(ss[k], r);
+    }
+    std::vector<double> dummy(5, 0.0);
+    UP(ss[0], dummy);
+#undef UP
+    const int64_t M = m.M, E = m.E;
+    const size_t MM = (size_t)M * M;
+    const size_t rs = A->fp64 ? 8 : 4;
+    if ((s = dev_alloc(A->rec, (size_t)E * E * sizeof(PairRec), st))) return bail(s);
+    if ((s = dev_alloc(A->wdlo, 3 * MM * sizeof(int16_t), st))) return bail(s);
+    if ((s = dev_alloc(A->wdhi, 3 * MM * sizeof(int16_t), st))) return bail(s);
+    if ((s = dev_alloc(A->wsmask, MM, st))) return bail(s);
+    if ((s = dev_alloc(A->dense, 3 * MM * A->KW * rs, st))) return bail(s);
+    if ((s = dev_alloc(A->dense_spec, NSPEC * MM * rs, st))) return bail(s);
+    if ((s = dev_alloc(A->ndense, (size_t)3 * M * m.NB * A->KW * sizeof(double), st))) return bail(s);
+    if ((s = dev_alloc(A->ndense_spec, (size_t)NSPEC * M * m.NB * sizeof(double), st))) return bail(s);
+    if ((s = dev_alloc(A->status, 16, st))) return bail(s);
+    const size_t nb = A->blocks.size();
+    if ((s = dev_alloc(A->cnt_far, nb * M * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->cnt_near, nb * M * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->rp_far, nb * (M + 1) * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->rp_near, nb * (M + 1) * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->tot_far, nb * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->tot_near, nb * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->off_far_d, nb * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->off_near_d, nb * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->quad_partial, 1024 * sizeof(int64_t), st))) return bail(s);
+    CUDA_TRY(cudaStreamSynchronize(st));
+    A->nnz_far.assign(nb, -1);
+    A->nnz_near.assign(nb, -1);
+    *out = A;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_num_blocks(const tdbem_asm *a, int64_t *n) {
+    if (!a || !n) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    *n = (int64_t)a->blocks.size();
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t *i, int32_t *m2, int32_t *m1,
+                              int64_t *nf, int64_t *nn) {
+    if (!a) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (b < 0 || b >= (int64_t)a->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
+    if (k) *k = a->blocks[b].kb;
+    if (i) *i = a->blocks[b].ib;
+    if (m2) *m2 = 0;
+    if (m1) *m1 = 0;
+    if (nf) *nf = a->nnz_far[b];
+    if (nn) *nn = a->nnz_near[b];
+    return TDBEM_OK;
+}
+
+static Geo make_geo(tdbem_asm *A) {
+    Geo g;
+    g.M = A->mesh->M; g.E = A->mesh->E;
+    g.F = (const int32_t *)A->F.p; g.cen = (const double *)A->cen.p; g.dq = (const double *)A->dq.p;
+    g.dq32 = (const float *)A->dq32.p; g.V = (const double *)A->V.p; g.geo32 = (const float *)A->geo32.p;
+    g.geo64 = (const double *)A->geo64.p; g.vt_ptr = (const int64_t *)A->vt_ptr.p; g.vt_tri = (const int32_t *)A->vt_tri.p;
+    return g;
+}
+
+static LagTables make_lt(tdbem_asm *A) {
+    LagTables lt;
+    int off = 0;
+    for (int c = 0; c < NCLASS; ++c) {
+        lt.a[c] = (const double *)A->lagA.p + off;
+        lt.b[c] = (const double *)A->lagB.p + off;
+        off += (int)A->lag_a[c].size();
+        lt.dlo[c] = A->cls_dlo[c];
+        lt.dhi[c] = A->cls_dhi[c];
+        lt.rho[c] = A->cls_rho[c];
+        lt.P[c] = A->cls_P[c];
+    }
+    lt.dt = A->tg->dt;
+    lt.inv_dt = 1.0 / A->tg->dt;
+    return lt;
+}
+
+tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
+    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    cudaStream_t st = (cudaStream_t)stream;
+    const tdbem_mesh &m = *A->mesh;
+    const int64_t M = m.M, E = m.E;
+    const size_t MM = (size_t)M * M;
+    const size_t rs = A->fp64 ? 8 : 4;
+    const size_t nb = A->blocks.size();
+    cudaEvent_t ev[6];
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(ev[0], st));
+    CUDA_TRY(cudaMemsetAsync(A->status.p, 0, 16, st));
+    CUDA_TRY(cudaMemsetAsync(A->dense.p, 0, A->dense.n, st));
+    CUDA_TRY(cudaMemsetAsync(A->dense_spec.p, 0, A->dense_spec.n, st));
+    CUDA_TRY(cudaMemsetAsync(A->ndense.p, 0, A->ndense.n, st));
+    CUDA_TRY(cudaMemsetAsync(A->ndense_spec.p, 0, A->ndense_spec.n, st));
+    // ---- psi tables (FP64 samples, Chebyshev coefficients)
+    const int n1 = TOTAL_PANELS, n4 = TOTAL_PANELS * A->S64;
+    launch_psi_samples((const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p,
+                       (const int *)A->tab_ib.p, (const double *)A->tab_r0.p, A->tg->dt, 1, n1,
+                       (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 8, (double *)A->tab_samples.p, st);
+    launch_psi_dct((const double *)A->tab_samples.p, n1, (double *)A->tab_coef1.p, st);
+    launch_psi_samples((const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p + n1,
+                       (const int *)A->tab_ib.p + n1, (const double *)A->tab_r0.p + n1, A->tg->dt / A->S64, A->S64,
+                       n4, (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 8,
+                       (double *)A->tab_samples.p + (size_t)n1 * NCHEB * 2, st);
+    launch_psi_dct((const double *)A->tab_samples.p + (size_t)n1 * NCHEB * 2, n4, (double *)A->tab_coef4.p, st);
+    CUDA_TRY(cudaGetLastError());
+    {
+        std::vector<double> c1((size_t)n1 * NCHEB * 2);
+        CUDA_TRY(cudaMemcpyAsync(c1.data(), A->tab_coef1.p, c1.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int p = 0; p < n1; ++p)
+            for (int n = 0; n < NCHEB; ++n)
+                for (int k = 0; k < 2; ++k) A->c32.c[p][n][k] = (float)c1[((size_t)p * NCHEB + n) * 2 + k];
+    }
+    // ---- element-pair bounds, vertex-pair windows
+    Geo g = make_geo(A);
+    LagTables lt = make_lt(A);
+    launch_pair_bounds(g, lt, (PairRec *)A->rec.p, st);
+    launch_vertex_windows(g, (const PairRec *)A->rec.p, (int16_t *)A->wdlo.p, (int16_t *)A->wdhi.p,
+                          (uint8_t *)A->wsmask.p, A->KW, (int *)A->status.p, st);
+    {
+        const int npp[4] = {49, A->ss_npp[1], A->ss_npp[2], A->ss_npp[3]};
+        launch_count_quad(g, (const PairRec *)A->rec.p, npp, (int64_t *)A->quad_partial.p, 1024, st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(ev[1], st));
+    // ---- far field, one launch per colour
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    for (size_t c = 0; c + 1 < A->color_off.size(); ++c) {
+        FarArgs fa;
+        fa.g = g; fa.lt = lt;
+        fa.dlo = (const int16_t *)A->wdlo.p; fa.dhi = (const int16_t *)A->wdhi.p; fa.smask = (const uint8_t *)A->wsmask.p;
+        fa.color_tris = (const int32_t *)A->colors.p + A->color_off[c];
+        fa.ncolor = A->color_off[c + 1] - A->color_off[c];
+        fa.chunk_vptr = (const int32_t *)A->chunk_vptr.p; fa.chunk_vert = (const int32_t *)A->chunk_vert.p;
+        fa.chunk_sptr = (const int32_t *)A->chunk_sptr.p; fa.chunk_src = (const int32_t *)A->chunk_src.p;
+        fa.nchunks = m.nchunks;
+        fa.rule_w = (const float *)A->rule_w.p; fa.rule_l = (const float *)A->rule_l.p;
+        fa.dense = A->dense.p; fa.dense_spec = A->dense_spec.p; fa.KW = A->KW;
+        fa.status = (int *)A->status.p;
+        fa.cheb64 = (const double *)A->tab_coef4.p;
+        const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)nsm);
+        if (grid > 0) launch_far(fa, A->c32, A->fp64, A->OFF, A->S64, grid, st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(ev[2], st));
+    // ---- near field, one launch per colour
+    for (size_t c = 0; c + 1 < A->color_off.size(); ++c) {
+        NearArgs na;
+        na.g = g; na.lt = lt;
+        na.dlo = (const int16_t *)A->wdlo.p; na.dhi = (const int16_t *)A->wdhi.p;
+        na.color_tris = (const int32_t *)A->colors.p + A->color_off[c];
+        na.ncolor = A->color_off[c + 1] - A->color_off[c];
+        na.adj_ptr = (const int64_t *)A->adj_ptr.p; na.adj_tri = (const int32_t *)A->adj_tri.p;
+        na.adj_perm = (const int8_t *)A->adj_perm.p; na.adj_nbr = (const int32_t *)A->adj_nbr.p;
+        na.rec = (const PairRec *)A->rec.p;
+        for (int k = 0; k < 4; ++k) { na.ss_xy[k] = (const double *)A->ss[k].p; na.ss_npp[k] = A->ss_npp[k]; }
+        na.cheb64 = (const double *)A->tab_coef4.p;
+        na.S = A->S64;
+        na.ndense = (double *)A->ndense.p; na.ndense_spec = (double *)A->ndense_spec.p;
+        na.NB = m.NB; na.KW = A->KW;
+        na.status = (int *)A->status.p;
+        const int grid = (int)std::min<int64_t>(na.ncolor, (int64_t)2 * nsm);
+        if (grid > 0) launch_near(na, grid, st);
+    }
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(ev[3], st));
+    // ---- CSR: row counts, offsets, sizes, fill
+    launch_row_counts2(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
+                       (const int *)A->cls_dlo_d.p, (const int *)A->cls_dhi_d.p, (const int *)A->blk_of_lag_d.p,
+                       (const int *)A->lag_base_d.p, (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p,
+                       (const int32_t *)A->nbr.p, (int64_t *)A->cnt_far.p, (int64_t *)A->cnt_near.p, st);
+    launch_scan_rows((const int64_t *)A->cnt_far.p, M, (int)nb, (int64_t *)A->rp_far.p, (int64_t *)A->tot_far.p, st);
+    launch_scan_rows((const int64_t *)A->cnt_near.p, M, (int)nb, (int64_t *)A->rp_near.p, (int64_t *)A->tot_near.p, st);
+    CUDA_TRY(cudaGetLastError());
+    A->nnz_far.assign(nb, 0);
+    A->nnz_near.assign(nb, 0);
+    std::vector<int64_t> qp(1024);
+    CUDA_TRY(cudaMemcpyAsync(A->nnz_far.data(), A->tot_far.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(A->nnz_near.data(), A->tot_near.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(qp.data(), A->quad_partial.p, 1024 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    A->off_far.assign(nb + 1, 0);
+    A->off_near.assign(nb + 1, 0);
+    for (size_t b = 0; b < nb; ++b) {
+        A->off_far[b + 1] = A->off_far[b] + A->nnz_far[b];
+        A->off_near[b + 1] = A->off_near[b] + A->nnz_near[b];
+    }
+    tdbem_status s;
+    if ((size_t)A->off_far[nb] > A->col_far_cap || A->col_far.p == nullptr) {
+        if ((s = dev_alloc(A->col_far, A->off_far[nb] * sizeof(int32_t), st))) return s;
+        if ((s = dev_alloc(A->val_far, A->off_far[nb] * rs, st))) return s;
+        A->col_far_cap = A->off_far[nb];
+    }
+    if ((size_t)A->off_near[nb] > A->col_near_cap || A->col_near.p == nullptr) {
+        if ((s = dev_alloc(A->col_near, A->off_near[nb] * sizeof(int32_t), st))) return s;
+        if ((s = dev_alloc(A->val_near, A->off_near[nb] * sizeof(double), st))) return s;
+        A->col_near_cap = A->off_near[nb];
+    }
+    CUDA_TRY(cudaMemcpyAsync(A->off_far_d.p, A->off_far.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(A->off_near_d.p, A->off_near.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
+                (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
+                (const int *)A->blk_of_spec_d.p, nullptr, nullptr, (const int64_t *)A->rp_far.p,
+                (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, A->dense.p, A->dense_spec.p, A->val_far.p,
+                A->KW, 0, A->fp64, st);
+    launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
+                (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
+                (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
+                (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
+                A->ndense.p, A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(ev[4], st));
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(&status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    float ms[4];
+    for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]));
+    for (auto &e : ev) cudaEventDestroy(e);
+    A->stats.n_blocks = (int64_t)nb;
+    A->stats.nnz = A->off_far[nb];
+    A->stats.nnz_near = A->off_near[nb];
+    int64_t q = 0;
+    for (int64_t v : qp) q += v;
+    A->stats.quad_points = q;
+    int64_t nearp = 0;
+    for (int64_t t = 0; t < E; ++t) nearp += m.adj_ptr[t + 1] - m.adj_ptr[t];
+    A->stats.near_pairs = nearp;
+    A->stats.far_pairs = E * E - nearp;
+    A->stats.ms_pattern = ms[0];
+    A->stats.ms_far = ms[1];
+    A->stats.ms_near = ms[2];
+    A->stats.ms_extract = ms[3];
+    A->stats.ms_total = ms[0] + ms[1] + ms[2] + ms[3];
+    if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
+    A->assembled = true;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_block_csr(const tdbem_asm *A, int64_t b, int32_t which, const int64_t **rp, const int32_t **col,
+                             const void **val, int64_t *nnz) {
+    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (b < 0 || b >= (int64_t)A->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    const int64_t M = A->mesh->M;
+    if (which == TDBEM_FAR) {
+        if (rp) *rp = (const int64_t *)A->rp_far.p + b * (M + 1);
+        if (col) *col = (const int32_t *)A->col_far.p + A->off_far[b];
+        if (val) *val = (const char *)A->val_far.p + A->off_far[b] * (A->fp64 ? 8 : 4);
+        if (nnz) *nnz = A->nnz_far[b];
+    } else if (which == TDBEM_NEAR) {
+        if (rp) *rp = (const int64_t *)A->rp_near.p + b * (M + 1);
+        if (col) *col = (const int32_t *)A->col_near.p + A->off_near[b];
+        if (val) *val = (const double *)A->val_near.p + A->off_near[b];
+        if (nnz) *nnz = A->nnz_near[b];
+    } else {
+        return fail(TDBEM_E_INVALID_ARG, "which must be TDBEM_FAR or TDBEM_NEAR");
+    }
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_block_csr_host(const tdbem_asm *A, int64_t b, int32_t which, int64_t *rp, int32_t *col,
+                                  void *val) {
+    const int64_t *drp;
+    const int32_t *dcol;
+    const void *dval;
+    int64_t nnz;
+    tdbem_status s = tdbem_block_csr(A, b, which, &drp, &dcol, &dval, &nnz);
+    if (s) return s;
+    const int64_t M = A->mesh->M;
+    const size_t vs = (which == TDBEM_FAR && !A->fp64) ? 4 : 8;
+    if (rp) CUDA_TRY(cudaMemcpy(rp, drp, (M + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (col && nnz) CUDA_TRY(cudaMemcpy(col, dcol, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (val && nnz) CUDA_TRY(cudaMemcpy(val, dval, nnz * vs, cudaMemcpyDeviceToHost));
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
+    if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    *out = A->stats;
+    return TDBEM_OK;
+}
+
+}  // extern "C"

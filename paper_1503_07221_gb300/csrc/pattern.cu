@@ -1,0 +1,396 @@
+// Culling and sparsity pattern (paper Sec. 3.2, Eq. SparsitySmallBlock):
+// element-pair distance bounds and kept lag ranges, vertex-pair lag windows,
+// per-block row counts, row offsets, and the CSR fill that gathers the
+// assembled values into per-block CSR.
+#include <math.h>
+
+#include "tdbem_internal.h"
+
+namespace tdbem {
+
+// ------------------------------------------------------------------ geometry
+struct d3 { double x, y, z; };
+__device__ static inline d3 ld3(const double *p) { return {p[0], p[1], p[2]}; }
+__device__ static inline d3 sub(d3 a, d3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ static inline d3 add(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ static inline d3 mul(d3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ static inline double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Squared distance from p to triangle (a,b,c): the closest point lies in one
+// of the seven Voronoi regions of the triangle (vertices, edges, interior).
+__device__ static double point_triangle_d2(d3 p, d3 a, d3 b, d3 c) {
+    const d3 ab = sub(b, a), ac = sub(c, a), ap = sub(p, a);
+    const double d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= 0.0 && d2 <= 0.0) return dot(ap, ap);
+    const d3 bp = sub(p, b);
+    const double d3_ = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3_ >= 0.0 && d4 <= d3_) return dot(bp, bp);
+    const double vc = d1 * d4 - d3_ * d2;
+    if (vc <= 0.0 && d1 >= 0.0 && d3_ <= 0.0) {
+        const d3 q = add(a, mul(ab, d1 / (d1 - d3_)));
+        const d3 e = sub(p, q);
+        return dot(e, e);
+    }
+    const d3 cp = sub(p, c);
+    const double d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= 0.0 && d5 <= d6) return dot(cp, cp);
+    const double vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+        const d3 q = add(a, mul(ac, d2 / (d2 - d6)));
+        const d3 e = sub(p, q);
+        return dot(e, e);
+    }
+    const double va = d3_ * d6 - d5 * d4;
+    if (va <= 0.0 && (d4 - d3_) >= 0.0 && (d5 - d6) >= 0.0) {
+        const d3 q = add(b, mul(sub(c, b), (d4 - d3_) / ((d4 - d3_) + (d5 - d6))));
+        const d3 e = sub(p, q);
+        return dot(e, e);
+    }
+    const double den = 1.0 / (va + vb + vc);
+    const d3 q = add(a, add(mul(ab, vb * den), mul(ac, vc * den)));
+    const d3 e = sub(p, q);
+    return dot(e, e);
+}
+
+__device__ static inline double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+// Squared distance between segments p0 + s (p1 - p0) and q0 + u (q1 - q0),
+// s, u in [0,1]: minimise over the square, clamping the unconstrained
+// minimiser and re-solving for the other parameter.
+__device__ static double segment_segment_d2(d3 p0, d3 p1, d3 q0, d3 q1) {
+    const d3 d1 = sub(p1, p0), d2 = sub(q1, q0), r = sub(p0, q0);
+    const double a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+    double s, u;
+    const double c = dot(d1, r), b = dot(d1, d2);
+    const double den = a * e - b * b;
+    s = den > 0.0 ? clamp01((b * f - c * e) / den) : 0.0;
+    u = (b * s + f) / e;
+    if (u < 0.0) { u = 0.0; s = clamp01(-c / a); }
+    else if (u > 1.0) { u = 1.0; s = clamp01((b - c) / a); }
+    const d3 w = sub(add(p0, mul(d1, s)), add(q0, mul(d2, u)));
+    return dot(w, w);
+}
+
+// ----------------------------------------------------------- bounds pass
+// Lowest lag in [lo, hi] with b_d > x (b increasing in d); hi + 1 if none.
+__device__ static int first_b_above(const double *b, int lo, int hi, double x) {
+    int L = lo, H = hi + 1;
+    while (L < H) {
+        const int m = (L + H) >> 1;
+        if (b[m - lo] > x) H = m; else L = m + 1;
+    }
+    return L;
+}
+// Highest lag in [lo, hi] with a_d < x (a increasing in d); lo - 1 if none.
+__device__ static int last_a_below(const double *a, int lo, int hi, double x) {
+    int L = lo - 1, H = hi;
+    while (L < H) {
+        const int m = (L + H + 1) >> 1;
+        if (a[m - lo] < x) L = m; else H = m - 1;
+    }
+    return L;
+}
+
+__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // trial
+    const int64_t q = blockIdx.y;                                       // test
+    if (s >= g.E) return;
+    const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
+    int shared = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) shared += (A[i] == B[j]);
+    d3 a[3], b[3];
+    for (int i = 0; i < 3; ++i) { a[i] = ld3(g.V + 3 * A[i]); b[i] = ld3(g.V + 3 * B[i]); }
+    double mx = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { const d3 d = sub(a[i], b[j]); mx = fmax(mx, dot(d, d)); }
+    const double dmax = sqrt(mx);
+    double dmin = 0.0;
+    if (!shared) {
+        double m2 = 1e300;
+        for (int i = 0; i < 3; ++i) {
+            m2 = fmin(m2, point_triangle_d2(a[i], b[0], b[1], b[2]));
+            m2 = fmin(m2, point_triangle_d2(b[i], a[0], a[1], a[2]));
+        }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                m2 = fmin(m2, segment_segment_d2(a[i], a[(i + 1) % 3], b[j], b[(j + 1) % 3]));
+        dmin = sqrt(m2);
+    }
+    PairRec r;
+    for (int c = 0; c < NLAG; ++c) {
+        r.lo[c] = 0; r.cnt[c] = 0;
+        if (lt.dlo[c] > lt.dhi[c]) continue;
+        const int lo = first_b_above(lt.b[c], lt.dlo[c], lt.dhi[c], dmin);
+        const int hi = last_a_below(lt.a[c], lt.dlo[c], lt.dhi[c], dmax);
+        if (lo <= hi) { r.lo[c] = (int16_t)lo; r.cnt[c] = (uint8_t)(hi - lo + 1); }
+    }
+    uint8_t sm = 0;
+    for (int c = NLAG; c < NCLASS; ++c) {
+        if (lt.dlo[c] > lt.dhi[c]) continue;
+        if (dmin < lt.b[c][0] && dmax > lt.a[c][0]) sm |= (uint8_t)(1u << (c - NLAG));
+    }
+    r.smask = sm;
+    r.adj = (uint8_t)shared;
+    for (int k = 0; k < 5; ++k) r.pad[k] = 0;
+    rec[q * g.E + s] = r;
+}
+
+void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st) {
+    dim3 grid((unsigned)((g.E + 127) / 128), (unsigned)g.E);
+    pair_bounds_kernel<<<grid, 128, 0, st>>>(g, lt, rec);
+}
+
+// --------------------------------------------------- vertex-pair windows
+// Window of vertex pair (l, j): union over tau in star(l), sigma in star(j)
+// of the element-pair lag ranges (an interval, since both stars are
+// connected). Layout [c][l][j]; an empty window has dlo > dhi.
+__global__ void vertex_windows_kernel(Geo g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
+                                      uint8_t *smask, int KW, int *status) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t l = blockIdx.y;
+    if (j >= g.M) return;
+    int lo[3] = {32767, 32767, 32767}, hi[3] = {-32768, -32768, -32768};
+    unsigned sm = 0;
+    for (int64_t x = g.vt_ptr[l]; x < g.vt_ptr[l + 1]; ++x) {
+        const int64_t tau = g.vt_tri[x];
+        for (int64_t y = g.vt_ptr[j]; y < g.vt_ptr[j + 1]; ++y) {
+            const PairRec r = rec[tau * g.E + g.vt_tri[y]];
+            for (int c = 0; c < 3; ++c)
+                if (r.cnt[c]) { lo[c] = min(lo[c], (int)r.lo[c]); hi[c] = max(hi[c], r.lo[c] + r.cnt[c] - 1); }
+            sm |= r.smask;
+        }
+    }
+    const int64_t MM = g.M * g.M;
+    for (int c = 0; c < 3; ++c) {
+        if (lo[c] <= hi[c] && hi[c] - lo[c] + 1 > KW) status[0] = ST_WINDOW;
+        dlo[c * MM + l * g.M + j] = (int16_t)lo[c];
+        dhi[c * MM + l * g.M + j] = (int16_t)hi[c];
+    }
+    smask[l * g.M + j] = (uint8_t)sm;
+}
+
+void launch_vertex_windows(const Geo &g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
+                           uint8_t *smask, int KW, int *status, cudaStream_t st) {
+    dim3 grid((unsigned)((g.M + 127) / 128), (unsigned)g.M);
+    vertex_windows_kernel<<<grid, 128, 0, st>>>(g, rec, dlo, dhi, smask, KW, status);
+}
+
+// ------------------------------------------ quadrature point-pair counter
+// sum over element pairs of (point pairs of its rule) x (kept blocks);
+// per-CTA partial sums, added up on the host (no atomics).
+__global__ void count_quad_kernel(Geo g, const PairRec *rec, int npp0, int npp1, int npp2,
+                                  int npp3, int64_t *partial) {
+    __shared__ int64_t red[256];
+    const int64_t n = g.E * g.E;
+    int64_t acc = 0;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const PairRec r = rec[x];
+        const int k = r.cnt[0] + r.cnt[1] + r.cnt[2] + __popc(r.smask);
+        const int npp = r.adj == 0 ? npp0 : (r.adj == 1 ? npp1 : (r.adj == 2 ? npp2 : npp3));
+        acc += (int64_t)k * npp;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+void launch_count_quad(const Geo &g, const PairRec *rec, const int *npp, int64_t *partial,
+                       int nblocks_grid, cudaStream_t st) {
+    count_quad_kernel<<<nblocks_grid, 256, 0, st>>>(g, rec, npp[0], npp[1], npp[2], npp[3], partial);
+}
+
+// ------------------------------------------------------------ row counts
+// One warp per (class, row). blockIdx.y = 0: far pattern over all columns,
+// 1: near sub-pattern over the row's neighbour list. Lag classes histogram
+// their window lags in shared memory; specials count their mask bits.
+constexpr int RC_WARPS = 8;
+constexpr int MAXLAG = 1024;
+
+__global__ void row_counts_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi,
+                                  const uint8_t *smask, const int *cls_dlo, const int *cls_dhi,
+                                  const int *blk_of_lag, const int *lag_base, const int *blk_of_spec,
+                                  const int64_t *nbr_ptr, const int32_t *nbr, int64_t *cnt_far,
+                                  int64_t *cnt_near) {
+    __shared__ int hist[RC_WARPS][MAXLAG];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = blockIdx.x * (int64_t)RC_WARPS + w;  // (c, l) with c in 0..3 (3 = specials)
+    const bool nearp = blockIdx.y == 1;
+    int64_t *cnt = nearp ? cnt_near : cnt_far;
+    if (item >= 4 * M) return;
+    const int c = (int)(item / M);
+    const int64_t l = item % M;
+    const int64_t MM = M * M;
+    const int64_t k0 = nearp ? nbr_ptr[l] : 0, k1 = nearp ? nbr_ptr[l + 1] : M;
+    if (c < 3) {
+        const int nl = cls_dhi[c] - cls_dlo[c] + 1;
+        if (nl <= 0) return;
+        for (int x = lane; x < nl; x += 32) hist[w][x] = 0;
+        __syncwarp();
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
+            const int64_t j = nearp ? nbr[k] : k;
+            const int a = dlo[c * MM + l * M + j], b = dhi[c * MM + l * M + j];
+            for (int d = a; d <= b; ++d) atomicAdd(&hist[w][d - cls_dlo[c]], 1);
+        }
+        __syncwarp();
+        for (int x = lane; x < nl; x += 32) {
+            const int blk = blk_of_lag[lag_base[c] + x];
+            cnt[(int64_t)blk * M + l] = hist[w][x];
+        }
+    } else {
+        int n[NSPEC] = {0, 0, 0, 0, 0};
+        for (int64_t k = k0 + lane; k < k1; k += 32) {
+            const int64_t j = nearp ? nbr[k] : k;
+            const unsigned m = smask[l * M + j];
+            for (int s = 0; s < NSPEC; ++s) n[s] += (m >> s) & 1u;
+        }
+        for (int s = 0; s < NSPEC; ++s) {
+            int v = n[s];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && blk_of_spec[s] >= 0) cnt[(int64_t)blk_of_spec[s] * M + l] = v;
+        }
+    }
+}
+
+void launch_row_counts2(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
+                        const int *cls_dlo, const int *cls_dhi, const int *blk_of_lag,
+                        const int *lag_base, const int *blk_of_spec, const int64_t *nbr_ptr,
+                        const int32_t *nbr, int64_t *cnt_far, int64_t *cnt_near, cudaStream_t st) {
+    dim3 grid((unsigned)((4 * M + RC_WARPS - 1) / RC_WARPS), 2);
+    row_counts_kernel<<<grid, RC_WARPS * 32, 0, st>>>(M, dlo, dhi, smask, cls_dlo, cls_dhi,
+                                                     blk_of_lag, lag_base, blk_of_spec, nbr_ptr,
+                                                     nbr, cnt_far, cnt_near);
+}
+
+// --------------------------------------------------------- row offset scan
+// One CTA per block: row_ptr[b][0..M] = exclusive scan of cnt[b][0..M-1].
+__global__ void scan_rows_kernel(const int64_t *cnt, int64_t M, int64_t *row_ptr, int64_t *totals) {
+    __shared__ int64_t sh[1024];
+    const int64_t b = blockIdx.x;
+    const int64_t *c = cnt + b * M;
+    int64_t *rp = row_ptr + b * (M + 1);
+    int64_t carry = 0;
+    for (int64_t base = 0; base < M; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < M ? c[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int64_t add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (i < M) rp[i] = carry + sh[threadIdx.x] - v;
+        const int64_t tot = sh[1023];
+        __syncthreads();
+        carry += tot;
+    }
+    if (threadIdx.x == 0) { rp[M] = carry; totals[b] = carry; }
+}
+
+void launch_scan_rows(const int64_t *cnt, int64_t M, int nsets, int64_t *row_ptr, int64_t *totals,
+                      cudaStream_t st) {
+    if (nsets <= 0) return;
+    scan_rows_kernel<<<nsets, 1024, 0, st>>>(cnt, M, row_ptr, totals);
+}
+
+// ---------------------------------------------------------------- CSR fill
+// One warp per (class, row); columns are visited in increasing order in
+// chunks of 32, and for every lag present in the chunk a ballot assigns the
+// positions, so each row comes out sorted by column.
+template <typename T>
+__global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
+                            const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
+                            const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
+                            const int64_t *row_ptr, const int64_t *blk_off, int32_t *col,
+                            const T *dense, const T *dense_spec, T *val, int KW, int NB) {
+    __shared__ int cur[RC_WARPS][MAXLAG];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = blockIdx.x * (int64_t)RC_WARPS + w;
+    if (item >= 4 * M) return;
+    const bool nearp = nbr_ptr != nullptr;
+    const int c = (int)(item / M);
+    const int64_t l = item % M;
+    const int64_t MM = M * M;
+    const int64_t k0 = nearp ? nbr_ptr[l] : 0, k1 = nearp ? nbr_ptr[l + 1] : M;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (c < 3) {
+        for (int x = lane; x < MAXLAG; x += 32) cur[w][x] = 0;
+        __syncwarp();
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            const bool ok = k < k1;
+            const int64_t j = ok ? (nearp ? nbr[k] : k) : 0;
+            int a = 32767, b = -32768;
+            if (ok) { a = dlo[c * MM + l * M + j]; b = dhi[c * MM + l * M + j]; }
+            int ca = a, cb = b;
+            for (int o = 16; o > 0; o >>= 1) {
+                ca = min(ca, __shfl_xor_sync(0xffffffffu, ca, o));
+                cb = max(cb, __shfl_xor_sync(0xffffffffu, cb, o));
+            }
+            for (int d = ca; d <= cb; ++d) {
+                const bool in = a <= d && d <= b;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (!bal) continue;
+                const int x = d - cls_dlo[c];
+                const int blk = blk_of_lag[lag_base[c] + x];
+                if (in) {
+                    const int64_t pos = blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] + cur[w][x] +
+                                        __popc(bal & lt_mask);
+                    col[pos] = (int32_t)j;
+                    const int64_t src = nearp ? ((c * M + l) * NB + (k - k0)) : (c * MM + l * M + j);
+                    val[pos] = dense[src * KW + (d - a)];
+                }
+                __syncwarp();
+                if (lane == 0) cur[w][x] += __popc(bal);
+                __syncwarp();
+            }
+        }
+    } else {
+        int64_t sc[NSPEC] = {0, 0, 0, 0, 0};
+        for (int64_t kb = k0; kb < k1; kb += 32) {
+            const int64_t k = kb + lane;
+            const bool ok = k < k1;
+            const int64_t j = ok ? (nearp ? nbr[k] : k) : 0;
+            const unsigned m = ok ? smask[l * M + j] : 0u;
+            for (int s = 0; s < NSPEC; ++s) {
+                const bool in = (m >> s) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (!bal) continue;
+                const int blk = blk_of_spec[s];
+                if (in && blk >= 0) {
+                    const int64_t pos = blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] + sc[s] +
+                                        __popc(bal & lt_mask);
+                    col[pos] = (int32_t)j;
+                    const int64_t src = nearp ? ((s * M + l) * NB + (k - k0)) : (s * MM + l * M + j);
+                    val[pos] = dense_spec[src];
+                }
+                sc[s] += __popc(bal);
+            }
+        }
+    }
+}
+
+void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
+                 const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
+                 const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
+                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const void *dense,
+                 const void *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st) {
+    const unsigned grid = (unsigned)((4 * M + RC_WARPS - 1) / RC_WARPS);
+    if (fp64)
+        fill_kernel<double><<<grid, RC_WARPS * 32, 0, st>>>(
+            M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
+            blk_off, col, (const double *)dense, (const double *)dense_spec, (double *)val, KW, NB);
+    else
+        fill_kernel<float><<<grid, RC_WARPS * 32, 0, st>>>(
+            M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
+            blk_off, col, (const float *)dense, (const float *)dense_spec, (float *)val, KW, NB);
+}
+
+}  // namespace tdbem

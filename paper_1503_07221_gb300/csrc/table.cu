@@ -1,0 +1,158 @@
+// psi / psi~ Chebyshev tables (paper Sec. 3.1): sample the time-convolved
+// basis functions of Eq. psis by a direct 1-D Gauss-Legendre quadrature on
+// the device (FP64), then transform the samples at Chebyshev points of the
+// first kind into coefficients.
+#include <math.h>
+
+#include "tdbem_internal.h"
+
+namespace tdbem {
+
+// Smooth step of Sec. 3: f(x) = erf(2 artanh x)/2 + 1/2 on |x| < 1, with
+// u = 2 artanh x:  f' = (2/sqrt(pi)) e^{-u^2} / (1 - x^2),
+//                  f'' = (4/sqrt(pi)) e^{-u^2} (x - 2u) / (1 - x^2)^2.
+__device__ static void smooth_step(double x, double &f0, double &f1, double &f2) {
+    if (x <= -1.0) { f0 = 0.0; f1 = 0.0; f2 = 0.0; return; }
+    if (x >= 1.0) { f0 = 1.0; f1 = 0.0; f2 = 0.0; return; }
+    const double u = 2.0 * atanh(x);
+    const double g = (1.0 - x) * (1.0 + x);
+    const double e = exp(-u * u);
+    const double k = 1.1283791670955126;  // 2 / sqrt(pi)
+    f0 = 0.5 * erfc(-u);
+    f1 = k * e / g;
+    f2 = 2.0 * k * e * (x - 2.0 * u) / (g * g);
+}
+
+// Rising cutoff f_j(s) = f(2 (s - t_j)/h - 1), h = t_{j+1} - t_j, and the
+// falling one 1 - f_j(s) = f(-(2 (s - t_j)/h - 1)), each with d/ds, d2/ds2.
+__device__ static void rising(double s, double tj, double h, double out[3]) {
+    double a, b, c;
+    smooth_step(2.0 * (s - tj) / h - 1.0, a, b, c);
+    out[0] = a; out[1] = b * 2.0 / h; out[2] = c * 4.0 / (h * h);
+}
+__device__ static void falling(double s, double tj, double h, double out[3]) {
+    double a, b, c;
+    smooth_step(1.0 - 2.0 * (s - tj) / h, a, b, c);
+    out[0] = a; out[1] = -b * 2.0 / h; out[2] = c * 4.0 / (h * h);
+}
+
+// Time basis function i (0-based) of Eq. BasisFunctions with p = 0 and its
+// first two derivatives at s; causal (zero for s < 0).
+//   i = 0:     8 mu_1 (s/h)^2,   mu_1 = 1 - f_0
+//   inner i:   mu_{i+1} = rho_i, rising on [t_{i-1}, t_i], falling on [t_i, t_{i+1}]
+//   i = N-1:   mu_N = f_{N-2} (1 beyond t_{N-1})
+__device__ static void basis(const double *t, int N, int i, double s, double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (s < 0.0) return;
+    double m[3];
+    if (i == 0) {
+        const double h = t[1] - t[0];
+        if (s >= t[1]) return;
+        falling(s, t[0], h, m);
+        const double q = s / h;
+        out[0] = 8.0 * m[0] * q * q;
+        out[1] = 8.0 * m[1] * q * q + 16.0 * m[0] * q / h;
+        out[2] = 8.0 * m[2] * q * q + 32.0 * m[1] * q / h + 16.0 * m[0] / (h * h);
+        return;
+    }
+    if (i == N - 1) {
+        if (s <= t[N - 2]) return;
+        if (s >= t[N - 1]) { out[0] = 1.0; return; }
+        rising(s, t[N - 2], t[N - 1] - t[N - 2], out);
+        return;
+    }
+    if (s <= t[i - 1] || s >= t[i + 1]) return;
+    if (s <= t[i]) rising(s, t[i - 1], t[i] - t[i - 1], out);
+    else falling(s, t[i], t[i + 1] - t[i], out);
+}
+
+__device__ static double left_end(const double *t, int N, int i) { return i == 0 ? 0.0 : t[i - 1]; }
+__device__ static double right_end(const double *t, int N, int i) { return i == N - 1 ? t[N - 1] : t[i + 1]; }
+
+// psi_{k,i}(r) and psi~_{k,i}(r) of Eq. psis: integrate over the overlap of
+// the test support and the shifted trial support, split at the interior
+// breakpoints t_k and t_i + r, composite Gauss-Legendre on each piece.
+__device__ static void psi_direct(const double *t, int N, int kb, int ib, double r,
+                                  const double *gx, const double *gw, int gn, int gsub,
+                                  double &psi, double &psit) {
+    psi = 0.0; psit = 0.0;
+    const double lo = fmax(left_end(t, N, kb), left_end(t, N, ib) + r);
+    const double hi = fmin(right_end(t, N, kb), right_end(t, N, ib) + r);
+    if (!(lo < hi)) return;
+    double br[4];
+    int nb = 0;
+    br[nb++] = lo;
+    if (kb > 0 && kb < N - 1 && t[kb] > lo && t[kb] < hi) br[nb++] = t[kb];
+    if (ib > 0 && ib < N - 1 && t[ib] + r > lo && t[ib] + r < hi) br[nb++] = t[ib] + r;
+    br[nb++] = hi;
+    if (nb == 4 && br[1] > br[2]) { double x = br[1]; br[1] = br[2]; br[2] = x; }
+    double s0 = 0.0, s1 = 0.0;
+    for (int p = 0; p + 1 < nb; ++p) {
+        const double a = br[p], w = (br[p + 1] - br[p]) / gsub;
+        if (!(w > 0.0)) continue;
+        for (int q = 0; q < gsub; ++q) {
+            const double a0 = a + q * w;
+            for (int g = 0; g < gn; ++g) {
+                const double tt = a0 + w * gx[g];
+                double bk[3], bi[3];
+                basis(t, N, kb, tt, bk);
+                basis(t, N, ib, tt - r, bi);
+                s0 += w * gw[g] * bi[2] * bk[1];
+                s1 += w * gw[g] * bi[0] * bk[1];
+            }
+        }
+    }
+    psi = s0;
+    psit = s1;
+}
+
+// One thread per (sub-panel, Chebyshev node). Sub-panel p covers
+// r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]).
+__global__ void psi_samples_kernel(const double *t, int N, const int *pkb, const int *pib,
+                                   const double *pr0, double dr, int total, const double *gx,
+                                   const double *gw, int gn, int gsub, double *samples) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total * NCHEB) return;
+    const int p = id / NCHEB, m = id % NCHEB;
+    const double xm = cos(M_PI * (m + 0.5) / NCHEB);
+    const double r = pr0[p] + 0.5 * dr * (xm + 1.0);
+    double a, b;
+    psi_direct(t, N, pkb[p], pib[p], r, gx, gw, gn, gsub, a, b);
+    samples[2 * id + 0] = a;
+    samples[2 * id + 1] = b;
+}
+
+// c_n = (2/K) sum_m f(x_m) cos(n pi (m + 1/2)/K), c_0 halved, K = NCHEB; the
+// panel is then f(x) = sum_n c_n T_n(x) with x in [-1, 1].
+__global__ void psi_dct_kernel(const double *samples, int total, double *coef) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= total * NCHEB) return;
+    const int p = id / NCHEB, n = id % NCHEB;
+    double s0 = 0.0, s1 = 0.0;
+    for (int m = 0; m < NCHEB; ++m) {
+        const double c = cos(M_PI * n * (m + 0.5) / NCHEB);
+        s0 += samples[2 * (p * NCHEB + m) + 0] * c;
+        s1 += samples[2 * (p * NCHEB + m) + 1] * c;
+    }
+    const double sc = (n == 0 ? 1.0 : 2.0) / NCHEB;
+    coef[2 * id + 0] = s0 * sc;
+    coef[2 * id + 1] = s1 * sc;
+}
+
+void launch_psi_samples(const double *t, int N, const int *panel_class, const int *panel_kb,
+                        const int *panel_ib, const double *panel_r0, double panel_dr, int S,
+                        int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
+                        double *samples, cudaStream_t st) {
+    (void)panel_class; (void)S;
+    const int n = total_sub * NCHEB;
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(t, N, panel_kb, panel_ib, panel_r0,
+                                                       panel_dr, total_sub, gl_x, gl_w, gl_n,
+                                                       gl_sub, samples);
+}
+
+void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st) {
+    const int n = total_sub * NCHEB;
+    psi_dct_kernel<<<(n + 127) / 128, 128, 0, st>>>(samples, total_sub, coef);
+}
+
+}  // namespace tdbem

@@ -1,0 +1,174 @@
+// Internal declarations of libtdbem: data layouts shared by the host planner
+// (api.cu) and the kernels (table.cu, pattern.cu, far.cu, near.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tdbem.h"
+
+namespace tdbem {
+
+// ---------------------------------------------------------------------------
+// Classes of unique blocks on an equidistant grid.
+//
+// Write F / I / L for the first, an inner and the last time basis function
+// (b_1, b_2..b_{N-1}, b_N in the paper's 1-based numbering). On an
+// equidistant grid psi_{k,i}(r) depends only on r - (k - i) dt for every
+// (test kind, trial kind) combination (Sec. 3.1, Eq. psiTildeRed and its
+// analogues for the boundary functions), so each combination is one class
+// with one prototype function Phi_c(q), q = r / dt, and the block of lag d
+// evaluates Phi_c(q - d). Its support is q - d in (rho_c, rho_c + P_c), cut
+// into P_c panels of unit width at the breakpoints of psi.
+//
+//   C1 (I test, F trial): blocks (d, 0),           d = 1..N-2, rho = -2, P = 3
+//   C2 (I, I):            blocks (i + d, i),       d = -1..N-3, rho = -2, P = 4
+//   C3 (L, I):            blocks (N-1, N-1-d),     d = 1..N-2, rho = -2, P = 3
+//   specials, one block each, lag 0:
+//   S00 (F,F) (0,0) rho 0 P 1;  S01 (F,I) (0,1) rho 0 P 1;
+//   SN0 (L,F) (N-1,0) rho N-3 P 2;  SNN (L,L) (N-1,N-1) rho 0 P 1;
+//   SN1N (I,L) (N-2,N-1) rho 0 P 1.
+// ---------------------------------------------------------------------------
+enum { C1 = 0, C2 = 1, C3 = 2, S00 = 3, S01 = 4, SN0 = 5, SNN = 6, SN1N = 7, NCLASS = 8 };
+constexpr int NLAG = 3;   // classes C1..C3 carry a range of lags
+constexpr int NSPEC = 5;  // the rest carry lag 0 only
+constexpr int NCHEB = 33; // Chebyshev coefficients per panel (degree 32)
+constexpr int MAXPANEL = 4;
+constexpr int TOTAL_PANELS = 3 + 4 + 3 + 1 + 1 + 2 + 1 + 1;  // sum of P_c = 16
+
+struct ClassDesc {
+    int rho;      // first panel starts at q - d = rho
+    int P;        // panels
+    int dlo, dhi; // lags of the blocks that exist (after the diam cut); dlo > dhi: none
+    int kb_rep, ib_rep, d_rep;  // block used to sample the prototype
+    int panel0;   // index of the class's first panel in the panel list
+};
+
+// Device-side view of everything the kernels read. Plain pointers only.
+struct Geo {
+    int64_t M, E;
+    const int32_t *F;       // E x 3
+    const double *cen;      // E x 3 centroids
+    const double *dq;       // E x 7 x 3 quadrature points minus centroid (FP64)
+    const float *dq32;      // same, FP32
+    const double *V;        // M x 3
+    const float *geo32;     // E x 16: n(3), area, curls(9), pad
+    const double *geo64;    // E x 16: same in FP64
+    const int64_t *vt_ptr;  // M + 1
+    const int32_t *vt_tri;  // triangles around a vertex
+};
+
+// Status word bits written by kernels (plain stores; any nonzero value fails the call)
+enum {
+    ST_OFF_RANGE = 1,      // a point pair fell outside the accumulator window
+    ST_WINDOW = 2,         // a vertex-pair lag window exceeded its storage
+    ST_NEAR_ORDER = 4,     // near rule too large for shared memory
+    ST_NBR = 8,            // near neighbour lookup failed
+};
+
+// Element-pair record of the bounds pass: kept lag range per lag class and a
+// bit mask of kept special blocks. cnt = 0 means no lag of that class.
+struct PairRec {
+    int16_t lo[3];
+    uint8_t cnt[3];
+    uint8_t smask;
+    uint8_t adj;   // number of shared vertices (0 far, 1 vertex, 2 edge, 3 same)
+    uint8_t pad[5];
+};
+static_assert(sizeof(PairRec) == 16, "PairRec is 16 bytes");
+
+// Per-class lag tables for the culling decisions (support endpoints computed
+// on the host from the time grid exactly as Sec. 3.2 states them).
+struct LagTables {
+    const double *a[NCLASS];  // a_d for d = dlo..dhi (index d - dlo)
+    const double *b[NCLASS];
+    int dlo[NCLASS], dhi[NCLASS];
+    int rho[NCLASS], P[NCLASS];
+    double dt, inv_dt;
+};
+
+// FP32 Chebyshev coefficients of all 16 panels (one sub-panel per unit),
+// passed by value so kernels read them from the constant bank.
+struct ChebF32 {
+    float c[TOTAL_PANELS][NCHEB][2];  // (psi, psi~)
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+// table.cu
+void launch_psi_samples(const double *t, int N, const int *panel_class, const int *panel_kb,
+                        const int *panel_ib, const double *panel_r0, double panel_dr, int S,
+                        int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
+                        double *samples, cudaStream_t st);
+void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st);
+
+// pattern.cu
+void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st);
+void launch_vertex_windows(const Geo &g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
+                           uint8_t *smask, int KW, int *status, cudaStream_t st);
+void launch_count_quad(const Geo &g, const PairRec *rec, const int *npp, int64_t *partial,
+                       int nblocks_grid, cudaStream_t st);
+void launch_row_counts2(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
+                        const int *cls_dlo, const int *cls_dhi, const int *blk_of_lag,
+                        const int *lag_base, const int *blk_of_spec, const int64_t *nbr_ptr,
+                        const int32_t *nbr, int64_t *cnt_far, int64_t *cnt_near, cudaStream_t st);
+void launch_scan_rows(const int64_t *cnt, int64_t M, int nsets, int64_t *row_ptr, int64_t *totals,
+                      cudaStream_t st);
+void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
+                 const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
+                 const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
+                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const void *dense,
+                 const void *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st);
+
+// far.cu
+struct FarArgs {
+    Geo g;
+    LagTables lt;
+    const int16_t *dlo;        // 3 x M x M vertex-pair window starts
+    const int16_t *dhi;
+    const uint8_t *smask;      // M x M special masks
+    const int32_t *color_tris; // triangles of the current colour
+    int64_t ncolor;
+    const int32_t *chunk_vptr; // per chunk of 32 triangles: vertex list offsets
+    const int32_t *chunk_vert;
+    const int32_t *chunk_sptr;
+    const int32_t *chunk_src;  // sigma_local * 3 + corner
+    int64_t nchunks;
+    const float *rule_w;       // 7 weights
+    const float *rule_l;       // 7 x 3 barycentrics
+    void *dense;               // 3 x M x M x KW  (float or double)
+    void *dense_spec;          // 5 x M x M
+    int KW;
+    int *status;
+    const double *cheb64;      // TOTAL_PANELS * S * NCHEB * 2 (FP64 path)
+};
+void launch_far(const FarArgs &a, const ChebF32 &c32, bool fp64, int off, int S, int grid,
+                cudaStream_t st);
+
+// near.cu
+struct NearArgs {
+    Geo g;
+    LagTables lt;
+    const int16_t *dlo;
+    const int16_t *dhi;
+    const int32_t *color_tris;
+    int64_t ncolor;
+    const int64_t *adj_ptr;   // per triangle: adjacent-pair list offsets
+    const int32_t *adj_tri;   // sigma
+    const int8_t *adj_perm;   // per adjacent pair: kase, pa[3], pb[3], pad
+    const int32_t *adj_nbr;   // per adjacent pair: 9 neighbour indices (a,b) of sigma's vertex in nbr(row)
+    const PairRec *rec;       // element-pair records of the bounds pass
+    const double *ss_xy[4];   // per kase 1..3: npp x 5 (xh0, xh1, yh0, yh1, w)
+    int ss_npp[4];
+    const double *cheb64;     // TOTAL_PANELS * S * NCHEB * 2
+    int S;
+    double *ndense;           // 3 x M x NB x KW
+    double *ndense_spec;      // 5 x M x NB
+    int NB, KW;
+    int *status;
+};
+void launch_near(const NearArgs &a, int grid, cudaStream_t st);
+
+}  // namespace tdbem

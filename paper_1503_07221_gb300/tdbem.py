@@ -1,0 +1,203 @@
+"""Python binding of libtdbem (argument marshalling only).
+
+Every function forwards to the C ABI declared in include/tdbem.h; all
+computation runs in the CUDA library. PyTorch supplies device memory (its
+caching allocator is registered as libtdbem's allocator) and the current CUDA
+stream. Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdbem.so")
+
+OK = 0
+PREC_FP64 = 0
+PREC_MIXED = 1
+FAR = 0
+NEAR = 1
+
+
+class TdbemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libtdbem error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("near_order", C.c_int32), ("cheb_degree", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_blocks", C.c_int64), ("nnz", C.c_int64), ("nnz_near", C.c_int64),
+                ("far_pairs", C.c_int64), ("near_pairs", C.c_int64), ("quad_points", C.c_int64),
+                ("ms_total", C.c_double), ("ms_pattern", C.c_double), ("ms_far", C.c_double),
+                ("ms_near", C.c_double), ("ms_extract", C.c_double)]
+
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_lib = None
+_cb = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libtdbem.so is not built (run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    L.tdbem_last_error.restype = C.c_char_p
+    L.tdbem_set_allocator.argtypes = [_ALLOC, _FREE, vp]
+    L.tdbem_mesh_create.argtypes = [vp, i64, vp, i64, C.POINTER(vp)]
+    L.tdbem_timegrid_create.argtypes = [vp, i64, i32, i32, C.c_double, C.POINTER(vp)]
+    L.tdbem_assembler_create.argtypes = [vp, vp, C.POINTER(Opts), vp, C.POINTER(vp)]
+    L.tdbem_num_blocks.argtypes = [vp, C.POINTER(i64)]
+    L.tdbem_block_info.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                   C.POINTER(i64), C.POINTER(i64)]
+    L.tdbem_assemble_all.argtypes = [vp, vp]
+    L.tdbem_block_csr.argtypes = [vp, i64, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+    L.tdbem_block_csr_host.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.tdbem_mesh_destroy.argtypes = [vp]
+    L.tdbem_timegrid_destroy.argtypes = [vp]
+    L.tdbem_asm_destroy.argtypes = [vp]
+    L.tdbem_mesh_destroy.restype = None
+    L.tdbem_timegrid_destroy.restype = None
+    L.tdbem_asm_destroy.restype = None
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects."""
+    return ["tdbem_last_error", "tdbem_set_allocator", "tdbem_mesh_create", "tdbem_timegrid_create",
+            "tdbem_assembler_create", "tdbem_num_blocks", "tdbem_block_info", "tdbem_assemble_all",
+            "tdbem_block_csr", "tdbem_block_csr_host", "tdbem_stats", "tdbem_mesh_destroy",
+            "tdbem_timegrid_destroy", "tdbem_asm_destroy"]
+
+
+def _check(code):
+    if code != OK:
+        raise TdbemError(code, lib().tdbem_last_error().decode())
+
+
+def use_torch_allocator():
+    """Route libtdbem's device allocations through torch's caching allocator."""
+    global _cb
+    import torch
+
+    def alloc(n, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(n))
+        except Exception:
+            return None
+
+    def free(p, stream, ctx):
+        torch.cuda.caching_allocator_delete(p)
+
+    _cb = (_ALLOC(alloc), _FREE(free))
+    _check(lib().tdbem_set_allocator(_cb[0], _cb[1], None))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(stream)
+
+
+class Mesh:
+    def __init__(self, verts, tris):
+        V = np.ascontiguousarray(verts, dtype=np.float64)
+        F = np.ascontiguousarray(tris, dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib().tdbem_mesh_create(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0], C.byref(h)))
+        self.h = h
+        self.M, self.E = V.shape[0], F.shape[0]
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tdbem_mesh_destroy(self.h)
+            self.h = None
+
+
+class TimeGrid:
+    def __init__(self, t, p=0, basis_kind=0, c=1.0):
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().tdbem_timegrid_create(t.ctypes.data, t.size, p, basis_kind, c, C.byref(h)))
+        self.h = h
+        self.N = t.size
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tdbem_timegrid_destroy(self.h)
+            self.h = None
+
+
+class Assembler:
+    """Unique blocks of the block-Hessenberg system of one mesh and time grid."""
+
+    def __init__(self, mesh: Mesh, grid: TimeGrid, precision=PREC_MIXED, near_order=4, stream=None):
+        o = Opts()
+        o.precision = precision
+        o.near_order = near_order
+        o.cheb_degree = 32
+        h = C.c_void_p()
+        _check(lib().tdbem_assembler_create(mesh.h, grid.h, C.byref(o), C.c_void_p(_stream(stream)), C.byref(h)))
+        self.h = h
+        self.mesh, self.grid = mesh, grid
+        self.precision = precision
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.tdbem_asm_destroy(self.h)
+            self.h = None
+
+    def assemble(self, stream=None):
+        _check(lib().tdbem_assemble_all(self.h, C.c_void_p(_stream(stream))))
+
+    def num_blocks(self):
+        n = C.c_int64()
+        _check(lib().tdbem_num_blocks(self.h, C.byref(n)))
+        return n.value
+
+    def block_info(self, b):
+        k, i, m2, m1 = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        nf, nn = C.c_int64(), C.c_int64()
+        _check(lib().tdbem_block_info(self.h, b, C.byref(k), C.byref(i), C.byref(m2), C.byref(m1),
+                                      C.byref(nf), C.byref(nn)))
+        return dict(k=k.value, i=i.value, m2=m2.value, m1=m1.value, nnz_far=nf.value, nnz_near=nn.value)
+
+    def blocks(self):
+        return [(d["k"], d["i"]) for d in (self.block_info(b) for b in range(self.num_blocks()))]
+
+    def block_csr_device(self, b, which=FAR):
+        rp, col, val = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        nnz = C.c_int64()
+        _check(lib().tdbem_block_csr(self.h, b, which, C.byref(rp), C.byref(col), C.byref(val), C.byref(nnz)))
+        return rp.value, col.value, val.value, nnz.value
+
+    def block_csr_host(self, b, which=FAR):
+        """(row_ptr int64[M+1], col int32[nnz], val) copied to host."""
+        info = self.block_info(b)
+        nnz = info["nnz_far"] if which == FAR else info["nnz_near"]
+        rp = np.zeros(self.mesh.M + 1, np.int64)
+        col = np.zeros(max(nnz, 1), np.int32)
+        vdt = np.float32 if (which == FAR and self.precision == PREC_MIXED) else np.float64
+        val = np.zeros(max(nnz, 1), vdt)
+        _check(lib().tdbem_block_csr_host(self.h, b, which, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rp, col[:nnz], val[:nnz]
+
+    def stats(self):
+        s = Stats()
+        _check(lib().tdbem_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in Stats._fields_}
