@@ -38,7 +38,9 @@
  *   - non-equidistant grids: f_i uses the local width t_{i+1}-t_i, the
  *     Legendre argument of an inner function uses t_i - t_{i-2}
  *   - support endpoints are open: a block keeps an entry iff mindist < b and
- *     maxdist > a (equality culls)
+ *     maxdist > a (equality culls); bounds within 1e-12 T of an endpoint
+ *     count as equal, since psi vanishes to all orders there and symmetric
+ *     meshes put exact ties on multiples of the time step
  *   - wave speed c = 1
  *
  * Exposed through a plain C ABI (ctypes) for the tests; see oracle.py.
@@ -122,6 +124,7 @@ typedef struct {
     int psi_mode;              /* 0 direct, 1 own interpolant */
     int interp_S, interp_n;
     double diam;
+    double tie;                /* support-endpoint tie band: 1e-12 T */
     int maxval;                /* maximum number of triangles at a vertex */
     /* unique blocks */
     int64_t nblk;
@@ -756,6 +759,7 @@ void *or_create(const double *V, int64_t M, const int32_t *F, int64_t E, const d
     P->F = (int32_t *)malloc(sizeof(int32_t) * 3 * E); memcpy(P->F, F, sizeof(int32_t) * 3 * E);
     P->t = (double *)malloc(sizeof(double) * N); memcpy(P->t, t, sizeof(double) * N);
     P->T = t[N - 1];
+    P->tie = 1e-12 * P->T;
     P->nrm = (double *)malloc(sizeof(double) * 3 * E);
     P->area = (double *)malloc(sizeof(double) * E);
     P->curl = (double *)malloc(sizeof(double) * 9 * E);
@@ -819,7 +823,7 @@ void *or_create(const double *V, int64_t M, const int32_t *F, int64_t E, const d
             double a, b;
             block_support(P, (int)k, (int)i, &a, &b);
             if (!(b > a)) continue;
-            if (a >= P->diam) continue;
+            if (a >= P->diam - P->tie) continue;
             for (int m2 = 0; m2 <= p; ++m2)
                 for (int m1 = 0; m1 <= p; ++m1) {
                     P->bk[P->nblk] = (int32_t)k; P->bi[P->nblk] = (int32_t)i;
@@ -1006,7 +1010,7 @@ static int64_t row_pattern(const orc_t *P, int64_t blk, const rowscratch *S, con
     block_support(P, P->bk[blk], P->bi[blk], &a, &b);
     int64_t c = 0;
     for (int64_t j = 0; j < P->M; ++j)
-        if (mind[j] < b && maxd[j] > a) { if (cols) cols[c] = (int32_t)j; ++c; }
+        if (mind[j] < b - P->tie && maxd[j] > a + P->tie) { if (cols) cols[c] = (int32_t)j; ++c; }
     (void)S;
     return c;
 }
@@ -1091,7 +1095,7 @@ void or_assemble_rows(void *h, const int64_t *rows, int64_t nrows, const int64_t
                     double dmn = S.dmin[k * P->E + q], dmx = S.dmax[k * P->E + q];
                     int nk = 0;
                     for (int64_t b = 0; b < nb; ++b)
-                        if (dmn < bb[b] && dmx > ba[b]) { kb[nk] = blks[b]; kidx[nk] = b; ++nk; }
+                        if (dmn < bb[b] - P->tie && dmx > ba[b] + P->tie) { kb[nk] = blks[b]; kidx[nk] = b; ++nk; }
                     if (nk == 0) continue;
                     memset(L, 0, sizeof(double) * 9 * nk);
                     int near = shared_vertices(P->F + 3 * s, P->F + 3 * q) > 0;

@@ -408,7 +408,7 @@ static tdbem_status plan_blocks(tdbem_asm &A) {
             const bool want = i == 0 || i == 1 || k == N - 1 || (k == 1 && i == 2) || (k == N - 2 && i == N - 1);
             if (!want || i > k + 1) continue;
             const double a = std::max(0.0, tl(k) - tr(i)), b = tr(k) - tl(i);
-            if (!(b > a) || a >= A.mesh->diam) continue;
+            if (!(b > a) || a >= A.mesh->diam - 1e-12 * T) continue;
             const int kk = kind_of(k, N), ki = kind_of(i, N);
             int cls, lag;
             if (kk == 1 && ki == 0) { cls = C1; lag = (int)k; }
@@ -700,6 +700,7 @@ static LagTables make_lt(tdbem_asm *A) {
     }
     lt.dt = A->tg->dt;
     lt.inv_dt = 1.0 / A->tg->dt;
+    lt.tie = 1e-12 * A->tg->T;
     return lt;
 }
 

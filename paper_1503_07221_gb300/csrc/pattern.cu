@@ -121,14 +121,15 @@ __global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
     for (int c = 0; c < NLAG; ++c) {
         r.lo[c] = 0; r.cnt[c] = 0;
         if (lt.dlo[c] > lt.dhi[c]) continue;
-        const int lo = first_b_above(lt.b[c], lt.dlo[c], lt.dhi[c], dmin);
-        const int hi = last_a_below(lt.a[c], lt.dlo[c], lt.dhi[c], dmax);
+        // kept iff dmin < b_d - tie and dmax > a_d + tie (open support, ties cull)
+        const int lo = first_b_above(lt.b[c], lt.dlo[c], lt.dhi[c], dmin + lt.tie);
+        const int hi = last_a_below(lt.a[c], lt.dlo[c], lt.dhi[c], dmax - lt.tie);
         if (lo <= hi) { r.lo[c] = (int16_t)lo; r.cnt[c] = (uint8_t)(hi - lo + 1); }
     }
     uint8_t sm = 0;
     for (int c = NLAG; c < NCLASS; ++c) {
         if (lt.dlo[c] > lt.dhi[c]) continue;
-        if (dmin < lt.b[c][0] && dmax > lt.a[c][0]) sm |= (uint8_t)(1u << (c - NLAG));
+        if (dmin < lt.b[c][0] - lt.tie && dmax > lt.a[c][0] + lt.tie) sm |= (uint8_t)(1u << (c - NLAG));
     }
     r.smask = sm;
     r.adj = (uint8_t)shared;

@@ -88,6 +88,7 @@ struct LagTables {
     int dlo[NCLASS], dhi[NCLASS];
     int rho[NCLASS], P[NCLASS];
     double dt, inv_dt;
+    double tie;  // support endpoints: bounds within tie of an endpoint count as equal (culled)
 };
 
 // FP32 Chebyshev coefficients of all 16 panels (one sub-panel per unit),
