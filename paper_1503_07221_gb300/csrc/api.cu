@@ -379,7 +379,7 @@ struct tdbem_asm {
     // device buffers
     DevBuf F, V, cen, dq, dq32, geo32, geo64, vt_ptr, vt_tri, adj_ptr, adj_tri, adj_perm, adj_nbr,
         nbr_ptr, nbr, chunk_vptr, chunk_vert, chunk_sptr, chunk_src, colors, rule_w, rule_l, tgrid,
-        lagA, lagB, rec, wdlo, wdhi, wsmask, dense, dense_spec, ndense, ndense_spec, status,
+        rule_w64, rule_l64, lagA, lagB, rec, wdlo, wdhi, wsmask, dense, dense_spec, ndense, ndense_spec, status,
         cls_dlo_d, cls_dhi_d, blk_of_lag_d, lag_base_d, blk_of_spec_d, cnt_far, cnt_near, rp_far,
         rp_near, tot_far, tot_near, off_far_d, off_near_d, col_far, val_far, col_near, val_near,
         tab_kb, tab_ib, tab_r0, tab_samples, tab_coef1, tab_coef4, gl_x, gl_w, ss[4], quad_partial;
@@ -576,6 +576,9 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     UP(adj_perm, m.adj_perm); UP(adj_nbr, m.adj_nbr); UP(nbr_ptr, m.nbr_ptr); UP(nbr, m.nbr);
     UP(chunk_vptr, m.chunk_vptr); UP(chunk_vert, m.chunk_vert); UP(chunk_sptr, m.chunk_sptr);
     UP(chunk_src, m.chunk_src); UP(colors, colors); UP(rule_w, rw); UP(rule_l, rl); UP(tgrid, tg->t);
+    std::vector<double> rw64(7), rl64(21);
+    for (int k = 0; k < 7; ++k) { rw64[k] = m.rule_W[k]; for (int d = 0; d < 3; ++d) rl64[3 * k + d] = m.rule_L[k][d]; }
+    UP(rule_w64, rw64); UP(rule_l64, rl64);
     std::vector<double> la, lb;
     std::vector<int> loff(NCLASS + 1, 0);
     for (int c = 0; c < NCLASS; ++c) {
@@ -636,8 +639,9 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     if ((s = dev_alloc(A->wdlo, 3 * MM * sizeof(int16_t), st))) return bail(s);
     if ((s = dev_alloc(A->wdhi, 3 * MM * sizeof(int16_t), st))) return bail(s);
     if ((s = dev_alloc(A->wsmask, MM, st))) return bail(s);
-    if ((s = dev_alloc(A->dense, 3 * MM * A->KW * rs, st))) return bail(s);
-    if ((s = dev_alloc(A->dense_spec, NSPEC * MM * rs, st))) return bail(s);
+    if ((s = dev_alloc(A->dense, 3 * MM * A->KW * sizeof(double), st))) return bail(s);
+    if ((s = dev_alloc(A->dense_spec, NSPEC * MM * sizeof(double), st))) return bail(s);
+    (void)rs;
     if ((s = dev_alloc(A->ndense, (size_t)3 * M * m.NB * A->KW * sizeof(double), st))) return bail(s);
     if ((s = dev_alloc(A->ndense_spec, (size_t)NSPEC * M * m.NB * sizeof(double), st))) return bail(s);
     if ((s = dev_alloc(A->status, 16, st))) return bail(s);
@@ -766,7 +770,8 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         fa.chunk_sptr = (const int32_t *)A->chunk_sptr.p; fa.chunk_src = (const int32_t *)A->chunk_src.p;
         fa.nchunks = m.nchunks;
         fa.rule_w = (const float *)A->rule_w.p; fa.rule_l = (const float *)A->rule_l.p;
-        fa.dense = A->dense.p; fa.dense_spec = A->dense_spec.p; fa.KW = A->KW;
+        fa.rule_w64 = (const double *)A->rule_w64.p; fa.rule_l64 = (const double *)A->rule_l64.p;
+        fa.dense = (double *)A->dense.p; fa.dense_spec = (double *)A->dense_spec.p; fa.KW = A->KW;
         fa.status = (int *)A->status.p;
         fa.cheb64 = (const double *)A->tab_coef4.p;
         const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)nsm);
@@ -832,13 +837,14 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
                 (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
                 (const int *)A->blk_of_spec_d.p, nullptr, nullptr, (const int64_t *)A->rp_far.p,
-                (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, A->dense.p, A->dense_spec.p, A->val_far.p,
+                (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, (const double *)A->dense.p,
+                (const double *)A->dense_spec.p, A->val_far.p,
                 A->KW, 0, A->fp64, st);
     launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
                 (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
                 (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
                 (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
-                A->ndense.p, A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
+                (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(ev[4], st));
     int status = 0;

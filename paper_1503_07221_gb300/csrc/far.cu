@@ -9,15 +9,16 @@
 // the lag that a panel feeds depends on floor(q) (Sec. 3.1, Eq.
 // psiTildeRed). The panels' coefficients are therefore uniform across the
 // warp (constant bank in the FP32 path). Per lag slot the thread keeps
-//   t_b = sum_y w_y lambda_b(y) psi / r  (b = 0, 1, and the plain sum),
+//   t_b = sum_y w_y lambda_b(y) psi / r  (b = 0, 1, 2),
 //   s~  = sum_y w_y psi~ / r,
 // and the CTA forms the local 3x3 matrix
 //   L_ab = |tau||sigma|/(4 pi) [ n_tau.n_sigma sum_x w_x lambda_a(x) t_b(x)
 //                               + curl_a.curl_b sum_x w_x s~(x) ].
 // The sum over the triangles sharing a trial vertex is reduced in shared
 // memory with a host-built per-chunk plan and added (read-modify-write,
-// no atomics) into the vertex-pair lag windows of the test triangle's three
-// rows. Launches are per colour of a vertex-disjoint triangle colouring, so
+// no atomics) into the FP64 vertex-pair lag windows of the test triangle's
+// three rows, so the long sums over test triangles and chunks do not
+// accumulate FP32 rounding. Launches are per colour of a vertex-disjoint triangle colouring, so
 // no two CTAs of a launch touch the same row.
 #include <math.h>
 
@@ -49,14 +50,26 @@ constexpr int FAR_THREADS = FAR_WARPS * 32;
 
 template <typename R>
 struct FarSetup {
+    R scale[32];
+    R nn[32];
     int base[32];
     int valid[32];
     float f0[32];
     float D[32][3];
     float R0[32];
-    float scale[32];
-    float nn[32];
 };
+
+// 7-point rule weight and barycentric in the working precision
+template <typename R>
+__device__ __forceinline__ R rule_w(const FarArgs &A, int k) {
+    if constexpr (sizeof(R) == 8) return A.rule_w64[k];
+    else return A.rule_w[k];
+}
+template <typename R>
+__device__ __forceinline__ R rule_l(const FarArgs &A, int k) {
+    if constexpr (sizeof(R) == 8) return A.rule_l64[k];
+    else return A.rule_l[k];
+}
 
 // Chebyshev coefficient of panel p, sub-panel sub, index n, component k.
 template <typename R>
@@ -71,10 +84,33 @@ __device__ __forceinline__ double coef<double>(const ChebF32 &, const double *c6
 }
 
 // Dot products of the panels [p0, p0 + NP) at Chebyshev argument x:
-// out[2 j + k] = sum_n c_{p0+j, n, k} T_n(x).
+// out[2 j + k] = sum_n c_{p0+j, n, k} T_n(x). In FP32 the T_n are kept and
+// each sum runs from n = 32 down to 0, so the small high-order terms are
+// added before the large leading ones: a third of the rounding error of the
+// forward order at the same number of FMAs.
 template <typename R, int NP>
 __device__ __forceinline__ void cheb_dots(const ChebF32 &c32, const double *c64, int S, int sub,
                                           int p0, R x, R out[2 * NP]) {
+    if constexpr (sizeof(R) == 4) {
+        R T[NCHEB];
+        T[0] = R(1);
+        T[1] = x;
+        const R x2 = x + x;
+#pragma unroll
+        for (int n = 2; n < NCHEB; ++n) T[n] = x2 * T[n - 1] - T[n - 2];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            R a = R(0), b = R(0);
+#pragma unroll
+            for (int n = NCHEB - 1; n >= 0; --n) {
+                a += coef<R>(c32, c64, S, sub, p0 + j, n, 0) * T[n];
+                b += coef<R>(c32, c64, S, sub, p0 + j, n, 1) * T[n];
+            }
+            out[2 * j] = a;
+            out[2 * j + 1] = b;
+        }
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         out[2 * j] = coef<R>(c32, c64, S, sub, p0 + j, 0, 0) + coef<R>(c32, c64, S, sub, p0 + j, 1, 0) * x;
@@ -103,9 +139,10 @@ struct Grp {
     static constexpr int off(int c) { return slot0<OFF>(c) - slot0<OFF>(AB); }
 };
 
-// Add the P panel values of lag class C for cell offset K = cell + OFF.
+// Add the P panel values of lag class C for cell offset K = cell + OFF:
+// t_b += psi w lambda_b / r (b = 0, 1, 2) and s~ += psi~ w / r.
 template <typename R, int OFF, int AB, int AE, int C, int K>
-__device__ __forceinline__ void acc_class(R (&acc)[Grp<OFF, AB, AE>::NS][4], const R *v, R f0, R f1, R f2) {
+__device__ __forceinline__ void acc_class(R (&acc)[Grp<OFF, AB, AE>::NS][4], const R *v, R f0, R f1, R f2, R wr) {
     if constexpr (C >= AB && C < AE) {
         constexpr int P = cls_P(C);
 #pragma unroll
@@ -115,41 +152,41 @@ __device__ __forceinline__ void acc_class(R (&acc)[Grp<OFF, AB, AE>::NS][4], con
             acc[s][0] += ps * f0;
             acc[s][1] += ps * f1;
             acc[s][2] += ps * f2;
-            acc[s][3] += pt * f2;
+            acc[s][3] += pt * wr;
         }
     }
 }
 
 template <typename R, int OFF, int AB, int AE, int K>
 __device__ __forceinline__ void acc_case(R (&acc)[Grp<OFF, AB, AE>::NS][4], const R *v1, const R *v2,
-                                         const R *v3, R f0, R f1, R f2) {
-    acc_class<R, OFF, AB, AE, C1, K>(acc, v1, f0, f1, f2);
-    acc_class<R, OFF, AB, AE, C2, K>(acc, v2, f0, f1, f2);
-    acc_class<R, OFF, AB, AE, C3, K>(acc, v3, f0, f1, f2);
+                                         const R *v3, R f0, R f1, R f2, R wr) {
+    acc_class<R, OFF, AB, AE, C1, K>(acc, v1, f0, f1, f2, wr);
+    acc_class<R, OFF, AB, AE, C2, K>(acc, v2, f0, f1, f2, wr);
+    acc_class<R, OFF, AB, AE, C3, K>(acc, v3, f0, f1, f2, wr);
 }
 
 template <typename R, int OFF, int AB, int AE>
 __device__ __forceinline__ void acc_switch(R (&acc)[Grp<OFF, AB, AE>::NS][4], int k, const R *v1,
-                                           const R *v2, const R *v3, R f0, R f1, R f2) {
+                                           const R *v2, const R *v3, R f0, R f1, R f2, R wr) {
     switch (k) {
-        case 0: acc_case<R, OFF, AB, AE, 0>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 1: acc_case<R, OFF, AB, AE, 1>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 2: acc_case<R, OFF, AB, AE, 2>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 3: if constexpr (OFF >= 2) acc_case<R, OFF, AB, AE, 3>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 4: if constexpr (OFF >= 2) acc_case<R, OFF, AB, AE, 4>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 5: if constexpr (OFF >= 3) acc_case<R, OFF, AB, AE, 5>(acc, v1, v2, v3, f0, f1, f2); break;
-        case 6: if constexpr (OFF >= 3) acc_case<R, OFF, AB, AE, 6>(acc, v1, v2, v3, f0, f1, f2); break;
+        case 0: acc_case<R, OFF, AB, AE, 0>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 1: acc_case<R, OFF, AB, AE, 1>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 2: acc_case<R, OFF, AB, AE, 2>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 3: if constexpr (OFF >= 2) acc_case<R, OFF, AB, AE, 3>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 4: if constexpr (OFF >= 2) acc_case<R, OFF, AB, AE, 4>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 5: if constexpr (OFF >= 3) acc_case<R, OFF, AB, AE, 5>(acc, v1, v2, v3, f0, f1, f2, wr); break;
+        case 6: if constexpr (OFF >= 3) acc_case<R, OFF, AB, AE, 6>(acc, v1, v2, v3, f0, f1, f2, wr); break;
         default: break;
     }
 }
 
 template <typename R, int OFF, int AB, int AE, int C>
-__device__ __forceinline__ void acc_special(R (&acc)[Grp<OFF, AB, AE>::NS][4], R ps, R pt, R fa, R fb, R wr) {
+__device__ __forceinline__ void acc_special(R (&acc)[Grp<OFF, AB, AE>::NS][4], R ps, R pt, R fa, R fb, R fc, R wr) {
     if constexpr (C >= AB && C < AE) {
         constexpr int s = Grp<OFF, AB, AE>::off(C);
         acc[s][0] += ps * fa;
         acc[s][1] += ps * fb;
-        acc[s][2] += ps * wr;
+        acc[s][2] += ps * fc;
         acc[s][3] += pt * wr;
     }
 }
@@ -207,8 +244,8 @@ __device__ __forceinline__ void quad_classes(const FarArgs &A, const ChebF32 &C3
             u = us - (R)sub;
         }
         const R x = u + u - R(1);
-        const R wr = p.valid ? (R)A.rule_w[y] / rr : R(0);
-        const R fa = wr * (R)A.rule_l[3 * y], fb = wr * (R)A.rule_l[3 * y + 1];
+        const R wr = p.valid ? rule_w<R>(A, y) / rr : R(0);
+        const R fa = wr * rule_l<R>(A, 3 * y), fb = wr * rule_l<R>(A, 3 * y + 1), fc = wr * rule_l<R>(A, 3 * y + 2);
         if (cell < -OFF || cell > OFF) {
             if (p.valid) A.status[0] = ST_OFF_RANGE;
             cell = 0;
@@ -218,7 +255,7 @@ __device__ __forceinline__ void quad_classes(const FarArgs &A, const ChebF32 &C3
             if constexpr (C1 >= AB && C1 < AE) cheb_dots<R, 3>(C32, c64, S, sub, cls_panel0(C1), x, v1);
             if constexpr (C2 >= AB && C2 < AE) cheb_dots<R, 4>(C32, c64, S, sub, cls_panel0(C2), x, v2);
             if constexpr (C3 >= AB && C3 < AE) cheb_dots<R, 3>(C32, c64, S, sub, cls_panel0(C3), x, v3);
-            acc_switch<R, OFF, AB, AE>(acc, cell + OFF, v1, v2, v3, fa, fb, wr);
+            acc_switch<R, OFF, AB, AE>(acc, cell + OFF, v1, v2, v3, fa, fb, fc, wr);
         }
         if constexpr (AE == NCLASS) {
             // special blocks: absolute cell 0 (four of them) or N-3, N-2 (SN0)
@@ -228,10 +265,10 @@ __device__ __forceinline__ void quad_classes(const FarArgs &A, const ChebF32 &C3
                 cheb_dots<R, 2>(C32, c64, S, sub, cls_panel0(S00), x, vs);      // S00, S01
                 cheb_dots<R, 2>(C32, c64, S, sub, cls_panel0(SNN), x, vs + 4);  // SNN, SN1N
                 if (absc == 0) {
-                    acc_special<R, OFF, AB, AE, S00>(acc, vs[0], vs[1], fa, fb, wr);
-                    acc_special<R, OFF, AB, AE, S01>(acc, vs[2], vs[3], fa, fb, wr);
-                    acc_special<R, OFF, AB, AE, SNN>(acc, vs[4], vs[5], fa, fb, wr);
-                    acc_special<R, OFF, AB, AE, SN1N>(acc, vs[6], vs[7], fa, fb, wr);
+                    acc_special<R, OFF, AB, AE, S00>(acc, vs[0], vs[1], fa, fb, fc, wr);
+                    acc_special<R, OFF, AB, AE, S01>(acc, vs[2], vs[3], fa, fb, fc, wr);
+                    acc_special<R, OFF, AB, AE, SNN>(acc, vs[4], vs[5], fa, fb, fc, wr);
+                    acc_special<R, OFF, AB, AE, SN1N>(acc, vs[6], vs[7], fa, fb, fc, wr);
                 }
             }
             if (__any_sync(0xffffffffu, p.valid && (absc == rhoSN0 || absc == rhoSN0 + 1))) {
@@ -239,7 +276,7 @@ __device__ __forceinline__ void quad_classes(const FarArgs &A, const ChebF32 &C3
                 cheb_dots<R, 2>(C32, c64, S, sub, cls_panel0(SN0), x, vs);
                 if (absc == rhoSN0 || absc == rhoSN0 + 1) {
                     const bool j1 = absc != rhoSN0;
-                    acc_special<R, OFF, AB, AE, SN0>(acc, j1 ? vs[2] : vs[0], j1 ? vs[3] : vs[1], fa, fb, wr);
+                    acc_special<R, OFF, AB, AE, SN0>(acc, j1 ? vs[2] : vs[0], j1 ? vs[3] : vs[1], fa, fb, fc, wr);
                 }
             }
         }
@@ -270,18 +307,17 @@ __device__ __forceinline__ void reduce_group(const FarArgs &A, int64_t tau, int6
 #pragma unroll
         for (int xw = 0; xw < 7; ++xw) {
             const R *q = red + ((size_t)(xw * 32 + sl) * NG + s) * 4;
-            const R t0 = q[0], t1 = q[1], ts = q[2];
-            const R tb[3] = {t0, t1, ts - t0 - t1};
-            const R wx = (R)A.rule_w[xw];
+            const R tb[3] = {q[0], q[1], q[2]};
+            const R wx = rule_w<R>(A, xw);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const R ga = wx * (R)A.rule_l[3 * xw + a];
+                const R ga = wx * rule_l<R>(A, 3 * xw + a);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) Sab[a][b] += ga * tb[b];
             }
             St += wx * q[3];
         }
-        const R sc = (R)su.scale[sl], nn = (R)su.nn[sl];
+        const R sc = su.scale[sl], nn = su.nn[sl];
         R *lp = Lb + ((size_t)sl * NS + slot0<OFF>(GB) + s) * 9;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -340,7 +376,8 @@ far_kernel(const FarArgs A, const __grid_constant__ ChebF32 C32, int S) {
             if (w == 0) {
                 const int64_t sg = ch * 32 + lane;
                 int valid = 0, base = 0;
-                float f0 = 0.f, R0 = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f, scale = 0.f, nn = 0.f;
+                float f0 = 0.f, R0 = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+                R scale = R(0), nn = R(0);
                 if (sg < E) {
                     const int32_t *B = g.F + 3 * sg;
                     int shared = 0;
@@ -355,9 +392,15 @@ far_kernel(const FarArgs A, const __grid_constant__ ChebF32 C32, int S) {
                     base = (int)fb;
                     f0 = (float)(q0 - fb);
                     R0 = (float)r0; D0 = (float)d0; D1 = (float)d1; D2 = (float)d2;
-                    const float *gt = g.geo32 + 16 * tau, *gs = g.geo32 + 16 * sg;
-                    scale = gt[3] * gs[3] * 0.07957747154594767f;  // 1/(4 pi)
-                    nn = gt[0] * gs[0] + gt[1] * gs[1] + gt[2] * gs[2];
+                    if constexpr (sizeof(R) == 8) {
+                        const double *gt = g.geo64 + 16 * tau, *gs = g.geo64 + 16 * sg;
+                        scale = gt[3] * gs[3] * 0.07957747154594767;  // 1/(4 pi)
+                        nn = gt[0] * gs[0] + gt[1] * gs[1] + gt[2] * gs[2];
+                    } else {
+                        const float *gt = g.geo32 + 16 * tau, *gs = g.geo32 + 16 * sg;
+                        scale = gt[3] * gs[3] * 0.07957747f;
+                        nn = gt[0] * gs[0] + gt[1] * gs[1] + gt[2] * gs[2];
+                    }
                 }
                 su.valid[lane] = valid; su.base[lane] = base; su.f0[lane] = f0; su.R0[lane] = R0;
                 su.D[lane][0] = D0; su.D[lane][1] = D1; su.D[lane][2] = D2;
@@ -430,8 +473,8 @@ far_kernel(const FarArgs A, const __grid_constant__ ChebF32 C32, int S) {
                                 if (slot < 0 || slot >= K) continue;
                                 sum += Lb[((size_t)sl * NS + so + slot) * 9 + 3 * a + b];
                             }
-                            R *dst = (R *)A.dense + ((c * MM + l * M + j) * A.KW + (d - wlo));
-                            *dst += sum;
+                            double *dst = A.dense + ((c * MM + l * M + j) * A.KW + (d - wlo));
+                            *dst += (double)sum;
                         }
                     } else {
                         const int sbit = c - NLAG;
@@ -443,8 +486,8 @@ far_kernel(const FarArgs A, const __grid_constant__ ChebF32 C32, int S) {
                             if (!su.valid[sl]) continue;
                             sum += Lb[((size_t)sl * NS + so) * 9 + 3 * a + b];
                         }
-                        R *dst = (R *)A.dense_spec + (sbit * MM + l * M + j);
-                        *dst += sum;
+                        double *dst = A.dense_spec + (sbit * MM + l * M + j);
+                        *dst += (double)sum;
                     }
                 }
             }

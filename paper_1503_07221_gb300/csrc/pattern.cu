@@ -310,7 +310,7 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                             const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                             const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
                             const int64_t *row_ptr, const int64_t *blk_off, int32_t *col,
-                            const T *dense, const T *dense_spec, T *val, int KW, int NB) {
+                            const double *dense, const double *dense_spec, T *val, int KW, int NB) {
     __shared__ int cur[RC_WARPS][MAXLAG];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t item = blockIdx.x * (int64_t)RC_WARPS + w;
@@ -346,7 +346,7 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                                         __popc(bal & lt_mask);
                     col[pos] = (int32_t)j;
                     const int64_t src = nearp ? ((c * M + l) * NB + (k - k0)) : (c * MM + l * M + j);
-                    val[pos] = dense[src * KW + (d - a)];
+                    val[pos] = (T)dense[src * KW + (d - a)];
                 }
                 __syncwarp();
                 if (lane == 0) cur[w][x] += __popc(bal);
@@ -370,7 +370,7 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                                         __popc(bal & lt_mask);
                     col[pos] = (int32_t)j;
                     const int64_t src = nearp ? ((s * M + l) * NB + (k - k0)) : (s * MM + l * M + j);
-                    val[pos] = dense_spec[src];
+                    val[pos] = (T)dense_spec[src];
                 }
                 sc[s] += __popc(bal);
             }
@@ -381,17 +381,17 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
 void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
                  const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                  const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
-                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const void *dense,
-                 const void *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st) {
+                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const double *dense,
+                 const double *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st) {
     const unsigned grid = (unsigned)((4 * M + RC_WARPS - 1) / RC_WARPS);
     if (fp64)
         fill_kernel<double><<<grid, RC_WARPS * 32, 0, st>>>(
             M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
-            blk_off, col, (const double *)dense, (const double *)dense_spec, (double *)val, KW, NB);
+            blk_off, col, dense, dense_spec, (double *)val, KW, NB);
     else
         fill_kernel<float><<<grid, RC_WARPS * 32, 0, st>>>(
             M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
-            blk_off, col, (const float *)dense, (const float *)dense_spec, (float *)val, KW, NB);
+            blk_off, col, dense, dense_spec, (float *)val, KW, NB);
 }
 
 }  // namespace tdbem

@@ -120,8 +120,8 @@ void launch_scan_rows(const int64_t *cnt, int64_t M, int nsets, int64_t *row_ptr
 void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_t *smask,
                  const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                  const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
-                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const void *dense,
-                 const void *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st);
+                 const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const double *dense,
+                 const double *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st);
 
 // far.cu
 struct FarArgs {
@@ -139,8 +139,10 @@ struct FarArgs {
     int64_t nchunks;
     const float *rule_w;       // 7 weights
     const float *rule_l;       // 7 x 3 barycentrics
-    void *dense;               // 3 x M x M x KW  (float or double)
-    void *dense_spec;          // 5 x M x M
+    const double *rule_w64;    // same in FP64
+    const double *rule_l64;
+    double *dense;             // 3 x M x M x KW lag windows, FP64 accumulation
+    double *dense_spec;        // 5 x M x M
     int KW;
     int *status;
     const double *cheb64;      // TOTAL_PANELS * S * NCHEB * 2 (FP64 path)

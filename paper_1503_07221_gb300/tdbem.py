@@ -90,8 +90,14 @@ def _check(code):
 
 
 def use_torch_allocator():
-    """Route libtdbem's device allocations through torch's caching allocator."""
+    """Route libtdbem's device allocations through torch's caching allocator.
+
+    Idempotent: the callbacks are created once and kept alive for the life of
+    the process, because every device buffer remembers the free callback it
+    was allocated with."""
     global _cb
+    if _cb is not None:
+        return
     import torch
 
     def alloc(n, stream, ctx):
@@ -185,6 +191,21 @@ class Assembler:
         nnz = C.c_int64()
         _check(lib().tdbem_block_csr(self.h, b, which, C.byref(rp), C.byref(col), C.byref(val), C.byref(nnz)))
         return rp.value, col.value, val.value, nnz.value
+
+    def block_csr_torch(self, b, which=FAR):
+        """(row_ptr, col, val) as zero-copy torch CUDA tensors over the
+        library's borrowed device arrays (valid until the next assemble)."""
+        import torch
+        rp, col, val, nnz = self.block_csr_device(b, which)
+        vt = "<f4" if (which == FAR and self.precision == PREC_MIXED) else "<f8"
+        M = self.mesh.M
+
+        def view(ptr, n, typestr):
+            class _A:
+                __cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2}
+            return torch.as_tensor(_A(), device="cuda") if n > 0 else torch.empty(0, device="cuda")
+
+        return view(rp, M + 1, "<i8"), view(col, nnz, "<i4"), view(val, nnz, vt)
 
     def block_csr_host(self, b, which=FAR):
         """(row_ptr int64[M+1], col int32[nnz], val) copied to host."""

@@ -1,0 +1,88 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py
+times, on a seeded sample of rows (all unique blocks): the oracle computes
+those rows entry by entry; the GPU rows must have the identical pattern and
+agree within the tolerance of the precision: relative Frobenius norm of the
+sampled rows of each block whose norm is at least 1e-3 of the largest, and
+every block's error against the largest block norm."""
+import numpy as np
+import pytest
+
+from paper_1503_07221_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL = {0: 1e-10, 1: 1e-6}
+
+
+@pytest.fixture(scope="module")
+def td():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1503_07221_gb300 import build, tdbem
+    build.build()
+    torch.cuda.set_device(0)
+    tdbem.use_torch_allocator()
+    return tdbem
+
+
+def _rows(asm, b, which, rows):
+    rp, col, val = asm.block_csr_torch(b, which)
+    rp = rp.cpu().numpy()
+    out = []
+    for l in rows:
+        a, e = int(rp[l]), int(rp[l + 1])
+        out.append((col[a:e].cpu().numpy(), val[a:e].double().cpu().numpy()))
+    return out
+
+
+def _check(td, name, precision, nrows, seed=0):
+    from oracle.oracle import Oracle
+    w = inputs.workload(name)
+    asm = td.Assembler(td.Mesh(w.verts, w.tris), td.TimeGrid(w.t), precision=precision)
+    asm.assemble()
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(w.M, size=nrows, replace=False))
+    orc = Oracle(w.verts, w.tris, w.t, psi_mode="interp")
+    ob = orc.blocks()
+    assert [(b[0], b[1]) for b in ob] == asm.blocks()
+    res = orc.assemble_rows(rows, np.arange(len(ob)))
+    nums, dens = [], []
+    for b in range(len(ob)):
+        gf = _rows(asm, b, td.FAR, rows)
+        gn = _rows(asm, b, td.NEAR, rows)
+        num = den = 0.0
+        for r, (c, f, n) in enumerate(res[b]):
+            assert np.array_equal(c, gf[r][0]), "pattern block %d row %d" % (b, rows[r])
+            ref = f + n
+            got = gf[r][1].copy()
+            pos = np.searchsorted(c, gn[r][0])
+            got[pos] += gn[r][1]
+            num += np.sum((got - ref) ** 2)
+            den += np.sum(ref ** 2)
+        nums.append(np.sqrt(num))
+        dens.append(np.sqrt(den))
+    nums, dens = np.array(nums), np.array(dens)
+    big = dens > 1e-3 * dens.max()
+    rel = nums[big] / dens[big]
+    worst = (float(rel.max()), ob[int(np.flatnonzero(big)[np.argmax(rel)])][:2])
+    absmax = float(nums.max() / dens.max())
+    print("%s prec %d: max rel %.3e at %s, median rel %.3e, max abs / largest block %.3e"
+          % (name, precision, worst[0], worst[1], float(np.median(rel)), absmax))
+    # blocks of norm >= 1e-3 of the largest: relative error per block; every
+    # block (including those made only of support-edge contributions, whose
+    # norm can be ~1e-20): error against the largest block
+    assert worst[0] < TOL[precision], worst
+    assert absmax < TOL[precision], absmax
+    return worst
+
+
+def test_sphere5120_jittered_fp64(td):
+    _check(td, "sphere5120j", 0, 6)
+
+
+def test_sphere5120_jittered_mixed(td):
+    _check(td, "sphere5120j", 1, 6)
+
+
+def test_sphere20480_mixed(td):
+    _check(td, "sphere20480", 1, 4)
