@@ -742,7 +742,11 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         CUDA_TRY(cudaStreamSynchronize(st));
         for (int p = 0; p < n1; ++p)
             for (int n = 0; n < NCHEB; ++n)
-                for (int k = 0; k < 2; ++k) A->c32.c[p][n][k] = (float)c1[((size_t)p * NCHEB + n) * 2 + k];
+                for (int k = 0; k < 2; ++k) {
+                    const double v = c1[((size_t)p * NCHEB + n) * 2 + k];
+                    A->c32.c[p][n][k] = (float)v;
+                    if (n < NCHEB_LO) A->c32.lo[p][n][k] = (float)(v - (double)(float)v);
+                }
     }
     // ---- element-pair bounds, vertex-pair windows
     Geo g = make_geo(A);

@@ -86,8 +86,11 @@ __device__ __forceinline__ double coef<double>(const ChebF32 &, const double *c6
 // Dot products of the panels [p0, p0 + NP) at Chebyshev argument x:
 // out[2 j + k] = sum_n c_{p0+j, n, k} T_n(x). In FP32 the T_n are kept and
 // each sum runs from n = 32 down to 0, so the small high-order terms are
-// added before the large leading ones: a third of the rounding error of the
-// forward order at the same number of FMAs.
+// added before the large leading ones (a third of the rounding error of the
+// forward order at the same number of FMAs), and it starts from the FP32
+// residuals of the leading coefficients: their rounding would otherwise be a
+// fixed perturbation of psi, which the quadrature does not average away and
+// the cancellation in the odd prototype amplifies.
 template <typename R, int NP>
 __device__ __forceinline__ void cheb_dots(const ChebF32 &c32, const double *c64, int S, int sub,
                                           int p0, R x, R out[2 * NP]) {
@@ -101,6 +104,11 @@ __device__ __forceinline__ void cheb_dots(const ChebF32 &c32, const double *c64,
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
             R a = R(0), b = R(0);
+#pragma unroll
+            for (int n = 0; n < NCHEB_LO; ++n) {
+                a += c32.lo[p0 + j][n][0] * T[n];
+                b += c32.lo[p0 + j][n][1] * T[n];
+            }
 #pragma unroll
             for (int n = NCHEB - 1; n >= 0; --n) {
                 a += coef<R>(c32, c64, S, sub, p0 + j, n, 0) * T[n];

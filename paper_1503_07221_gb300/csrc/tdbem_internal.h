@@ -93,8 +93,10 @@ struct LagTables {
 
 // FP32 Chebyshev coefficients of all 16 panels (one sub-panel per unit),
 // passed by value so kernels read them from the constant bank.
+constexpr int NCHEB_LO = 4;  // leading coefficients carried as a hi + lo float pair
 struct ChebF32 {
-    float c[TOTAL_PANELS][NCHEB][2];  // (psi, psi~)
+    float c[TOTAL_PANELS][NCHEB][2];      // (psi, psi~), rounded to FP32
+    float lo[TOTAL_PANELS][NCHEB_LO][2];  // c - (double)(float)c of the leading ones
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
