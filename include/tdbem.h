@@ -62,6 +62,13 @@
 extern "C" {
 #endif
 
+/* entry points are the only exported symbols of libtdbem.so */
+#if defined(__GNUC__)
+#define TDBEM_API __attribute__((visibility("default")))
+#else
+#define TDBEM_API
+#endif
+
 typedef int tdbem_status;
 #define TDBEM_OK 0
 #define TDBEM_E_INVALID_ARG 1   /* NULL pointer, size or option out of range */
@@ -110,12 +117,12 @@ typedef struct {
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */
-const char *tdbem_last_error(void);
+TDBEM_API const char *tdbem_last_error(void);
 
 /* Register device allocation callbacks (NULL, NULL restores cudaMalloc).
  * alloc(bytes, stream, ctx) returns a device pointer or NULL;
  * free_(ptr, stream, ctx) releases it. Applies to objects created later. */
-tdbem_status tdbem_set_allocator(void *(*alloc)(size_t, void *, void *),
+TDBEM_API tdbem_status tdbem_set_allocator(void *(*alloc)(size_t, void *, void *),
                                  void (*free_)(void *, void *, void *), void *ctx);
 
 /* Surface mesh: M vertices (host, M x 3 doubles, row-major) and E flat
@@ -123,7 +130,7 @@ tdbem_status tdbem_set_allocator(void *(*alloc)(size_t, void *, void *),
  * the side the unit normal points to). Each vertex carries one hat function
  * phi_j (Sec. 3, "piecewise linear"). Fails with TDBEM_E_MESH on an index out
  * of range, a repeated index, a zero-area triangle or a non-finite vertex. */
-tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, const int32_t *tris,
+TDBEM_API tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, const int32_t *tris,
                                int64_t E, tdbem_mesh **out);
 
 /* Time grid of N points (host): t[0] = 0 < t[1] < ... < t[N-1] = T (Sec. 3).
@@ -132,32 +139,32 @@ tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, const int32_t
  * |x-y|/c). An equidistant grid (|t_i - i T/(N-1)| <= 1e-12 T) uses the
  * Toeplitz block reuse of Sec. 5.1 and needs N >= 5; other grids are not
  * supported by this build (TDBEM_E_UNSUPPORTED). */
-tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t basis_kind,
+TDBEM_API tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t basis_kind,
                                    double c, tdbem_timegrid **out);
 
 /* Plan an assembler on the current CUDA device: the unique block list, the
  * device copies of the geometry and the triangle colouring. opts may be
  * NULL (defaults: MIXED, near_order 4, degree 32). */
-tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid *tg,
+TDBEM_API tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid *tg,
                                     const tdbem_opts *opts, void *stream, tdbem_asm **out);
 
 /* Number of unique blocks, and block b's test / trial time index (0-based),
  * temporal orders and structural entry counts (after an assemble call;
  * -1 before). */
-tdbem_status tdbem_num_blocks(const tdbem_asm *a, int64_t *n_unique);
-tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t *i,
+TDBEM_API tdbem_status tdbem_num_blocks(const tdbem_asm *a, int64_t *n_unique);
+TDBEM_API tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t *i,
                               int32_t *m2, int32_t *m1, int64_t *nnz_far, int64_t *nnz_near);
 
 /* Assemble every unique block: psi tables, element-pair bounds, vertex-pair
  * windows, far and near quadrature, CSR extraction. Synchronises the stream
  * at the end and returns TDBEM_E_DEVICE if a kernel flagged an inconsistency. */
-tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
+TDBEM_API tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
 
 /* CSR of unique block b (borrowed device pointers). which = TDBEM_FAR: M+1
  * int64 row offsets, int32 sorted columns and float (MIXED) / double (FP64)
  * values; TDBEM_NEAR: the near sub-pattern with double values. Any output
  * pointer may be NULL. */
-tdbem_status tdbem_block_csr(const tdbem_asm *a, int64_t b, int32_t which,
+TDBEM_API tdbem_status tdbem_block_csr(const tdbem_asm *a, int64_t b, int32_t which,
                              const int64_t **row_ptr_dev, const int32_t **col_dev,
                              const void **val_dev, int64_t *nnz);
 
@@ -165,15 +172,15 @@ tdbem_status tdbem_block_csr(const tdbem_asm *a, int64_t b, int32_t which,
  * (nnz int32) and val (nnz float for TDBEM_FAR in MIXED mode, else double),
  * sizes as reported by tdbem_block_csr / tdbem_block_info. Any buffer may be
  * NULL. Synchronous (device-wide cudaMemcpy). */
-tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32_t which, int64_t *rp,
+TDBEM_API tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32_t which, int64_t *rp,
                                   int32_t *col, void *val);
 
 /* Assembly counters and the per-phase device times of the last assembly. */
-tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
+TDBEM_API tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
 
-void tdbem_mesh_destroy(tdbem_mesh *m);
-void tdbem_timegrid_destroy(tdbem_timegrid *t);
-void tdbem_asm_destroy(tdbem_asm *a);
+TDBEM_API void tdbem_mesh_destroy(tdbem_mesh *m);
+TDBEM_API void tdbem_timegrid_destroy(tdbem_timegrid *t);
+TDBEM_API void tdbem_asm_destroy(tdbem_asm *a);
 
 #ifdef __cplusplus
 }

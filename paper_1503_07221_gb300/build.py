@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo",
-         "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fvisibility=hidden"]
 
 
 def nvcc() -> str:

@@ -563,6 +563,7 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     if (A->OFF < 1) A->OFF = 1;
     if (A->OFF > 3) return bail(fail(TDBEM_E_UNSUPPORTED, "triangles too large for the time step (2 max|x - c|/dt > 3)"));
     A->KW = 4 + (int)ceil(2.0 * mesh->max_star / dt) + 2;
+    if (A->KW > 16) return bail(fail(TDBEM_E_UNSUPPORTED, "vertex stars too large for the time step (lag window > 16)"));
     const tdbem_mesh &m = *mesh;
     // uploads
     std::vector<int32_t> colors;
@@ -778,8 +779,15 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         fa.dense = (double *)A->dense.p; fa.dense_spec = (double *)A->dense_spec.p; fa.KW = A->KW;
         fa.status = (int *)A->status.p;
         fa.cheb64 = (const double *)A->tab_coef4.p;
+        for (int k = 0; k < 7; ++k) {
+            fa.rw32[k] = (float)m.rule_W[k];
+            for (int d = 0; d < 3; ++d) fa.rl32[3 * k + d] = (float)m.rule_L[k][d];
+        }
         const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)nsm);
-        if (grid > 0) launch_far(fa, A->c32, A->fp64, A->OFF, A->S64, grid, st);
+        if (grid > 0) {
+            if (A->fp64) launch_far(fa, A->c32, true, A->OFF, A->S64, grid, st);
+            else launch_far32(fa, A->c32, A->OFF, grid, st);
+        }
     }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(ev[2], st));
@@ -799,8 +807,15 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         na.ndense = (double *)A->ndense.p; na.ndense_spec = (double *)A->ndense_spec.p;
         na.NB = m.NB; na.KW = A->KW;
         na.status = (int *)A->status.p;
+        na.far_spec = (double *)A->dense_spec.p;
+        na.smask = (const uint8_t *)A->wsmask.p;
+        na.rule_w64 = (const double *)A->rule_w64.p; na.rule_l64 = (const double *)A->rule_l64.p;
         const int grid = (int)std::min<int64_t>(na.ncolor, (int64_t)2 * nsm);
-        if (grid > 0) launch_near(na, grid, st);
+        if (grid > 0) {
+            launch_near(na, grid, st);
+            // mixed: the far pairs of the special blocks, FP64 (the FP32 kernel skips them)
+            if (!A->fp64) launch_farspec(na, (int)std::min<int64_t>(na.ncolor, (int64_t)8 * nsm), st);
+        }
     }
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(ev[3], st));

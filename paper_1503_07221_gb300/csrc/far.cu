@@ -22,54 +22,9 @@
 // no two CTAs of a launch touch the same row.
 #include <math.h>
 
-#include "tdbem_internal.h"
+#include "far_common.cuh"
 
 namespace tdbem {
-
-__host__ __device__ constexpr int cls_P(int c) {
-    return c == C1 ? 3 : c == C2 ? 4 : c == C3 ? 3 : c == SN0 ? 2 : 1;
-}
-__host__ __device__ constexpr int cls_panel0(int c) {
-    return c == C1 ? 0 : c == C2 ? 3 : c == C3 ? 7 : c == S00 ? 10 : c == S01 ? 11 : c == SN0 ? 12 : c == SNN ? 14 : 15;
-}
-// accumulator slots of class c: lag classes cover cell in [-OFF, OFF] and
-// their P panels; specials keep only lag 0
-template <int OFF>
-__host__ __device__ constexpr int cls_K(int c) { return c < NLAG ? 2 * OFF + cls_P(c) : 1; }
-template <int OFF>
-__host__ __device__ constexpr int slot0(int c) {
-    int s = 0;
-    for (int x = 0; x < c; ++x) s += cls_K<OFF>(x);
-    return s;
-}
-template <int OFF>
-__host__ __device__ constexpr int total_slots() { return slot0<OFF>(NCLASS); }
-
-constexpr int FAR_WARPS = 7;
-constexpr int FAR_THREADS = FAR_WARPS * 32;
-
-template <typename R>
-struct FarSetup {
-    R scale[32];
-    R nn[32];
-    int base[32];
-    int valid[32];
-    float f0[32];
-    float D[32][3];
-    float R0[32];
-};
-
-// 7-point rule weight and barycentric in the working precision
-template <typename R>
-__device__ __forceinline__ R rule_w(const FarArgs &A, int k) {
-    if constexpr (sizeof(R) == 8) return A.rule_w64[k];
-    else return A.rule_w[k];
-}
-template <typename R>
-__device__ __forceinline__ R rule_l(const FarArgs &A, int k) {
-    if constexpr (sizeof(R) == 8) return A.rule_l64[k];
-    else return A.rule_l[k];
-}
 
 // Chebyshev coefficient of panel p, sub-panel sub, index n, component k.
 template <typename R>
@@ -446,59 +401,7 @@ far_kernel(const FarArgs A, const __grid_constant__ ChebF32 C32, int S) {
                 }
             }
 
-            // ---- sum over the triangles of this chunk sharing a trial vertex,
-            //      add into the lag windows of rows F[tau][a]
-            {
-                const int v0 = A.chunk_vptr[ch], v1 = A.chunk_vptr[ch + 1];
-                const int nv = v1 - v0;
-                for (int it = threadIdx.x; it < nv * 3 * NCLASS; it += FAR_THREADS) {
-                    const int v = it / (3 * NCLASS), rem = it % (3 * NCLASS);
-                    const int a = rem / NCLASS, c = rem % NCLASS;
-                    const int64_t j = A.chunk_vert[v0 + v];
-                    const int64_t l = a == 0 ? Ft0 : (a == 1 ? Ft1 : Ft2);
-                    const int s0 = A.chunk_sptr[v0 + v], s1 = A.chunk_sptr[v0 + v + 1];
-                    if (c < NLAG) {
-                        const int P = cls_P(c), K = 2 * OFF + P;
-                        const int rho = A.lt.rho[c];
-                        const int so = c == C1 ? slot0<OFF>(C1) : c == C2 ? slot0<OFF>(C2) : slot0<OFF>(C3);
-                        int dmn = 1 << 30, dmx = -(1 << 30);
-                        for (int x = s0; x < s1; ++x) {
-                            const int sl = A.chunk_src[x] / 3;
-                            if (!su.valid[sl]) continue;
-                            const int dv = su.base[sl] - rho - (P - 1) - OFF;
-                            dmn = min(dmn, dv);
-                            dmx = max(dmx, dv + K - 1);
-                        }
-                        const int wlo = A.dlo[c * MM + l * M + j], whi = A.dhi[c * MM + l * M + j];
-                        dmn = max(dmn, wlo);
-                        dmx = min(min(dmx, whi), wlo + A.KW - 1);
-                        for (int d = dmn; d <= dmx; ++d) {
-                            R sum = R(0);
-                            for (int x = s0; x < s1; ++x) {
-                                const int src = A.chunk_src[x], sl = src / 3, b = src % 3;
-                                if (!su.valid[sl]) continue;
-                                const int slot = d - (su.base[sl] - rho - (P - 1) - OFF);
-                                if (slot < 0 || slot >= K) continue;
-                                sum += Lb[((size_t)sl * NS + so + slot) * 9 + 3 * a + b];
-                            }
-                            double *dst = A.dense + ((c * MM + l * M + j) * A.KW + (d - wlo));
-                            *dst += (double)sum;
-                        }
-                    } else {
-                        const int sbit = c - NLAG;
-                        if (!((A.smask[l * M + j] >> sbit) & 1u)) continue;
-                        const int so = slot0<OFF>(C3) + cls_K<OFF>(C3) + sbit;
-                        R sum = R(0);
-                        for (int x = s0; x < s1; ++x) {
-                            const int src = A.chunk_src[x], sl = src / 3, b = src % 3;
-                            if (!su.valid[sl]) continue;
-                            sum += Lb[((size_t)sl * NS + so) * 9 + 3 * a + b];
-                        }
-                        double *dst = A.dense_spec + (sbit * MM + l * M + j);
-                        *dst += (double)sum;
-                    }
-                }
-            }
+            scatter_chunk<R, OFF, FAR_THREADS>(A, ch, Ft0, Ft1, Ft2, su, Lb);
             __syncthreads();
         }
     }

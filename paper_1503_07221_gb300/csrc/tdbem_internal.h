@@ -143,6 +143,8 @@ struct FarArgs {
     const float *rule_l;       // 7 x 3 barycentrics
     const double *rule_w64;    // same in FP64
     const double *rule_l64;
+    float rw32[7];             // 7-point rule weights and barycentrics by value
+    float rl32[21];            // (constant bank in the FP32 kernel)
     double *dense;             // 3 x M x M x KW lag windows, FP64 accumulation
     double *dense_spec;        // 5 x M x M
     int KW;
@@ -151,6 +153,8 @@ struct FarArgs {
 };
 void launch_far(const FarArgs &a, const ChebF32 &c32, bool fp64, int off, int S, int grid,
                 cudaStream_t st);
+// far32.cu
+void launch_far32(const FarArgs &a, const ChebF32 &c32, int off, int grid, cudaStream_t st);
 
 // near.cu
 struct NearArgs {
@@ -171,9 +175,15 @@ struct NearArgs {
     int S;
     double *ndense;           // 3 x M x NB x KW
     double *ndense_spec;      // 5 x M x NB
+    double *far_spec;         // 5 x M x M far-pair special-block values (FP64)
+    const uint8_t *smask;     // M x M special masks of the vertex pairs
+    const double *rule_w64;   // 7-point rule weights and barycentrics
+    const double *rule_l64;
     int NB, KW;
     int *status;
 };
 void launch_near(const NearArgs &a, int grid, cudaStream_t st);
+// far element pairs that reach a special block, FP64 7-point rule
+void launch_farspec(const NearArgs &a, int grid, cudaStream_t st);
 
 }  // namespace tdbem
