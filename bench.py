@@ -189,8 +189,7 @@ def run_ours(args):
     value = nnz * world / (ms * 1e-3)
     qps = st["quad_points"] * world / (ms * 1e-3)
     nb = st["n_blocks"]
-    ncol = None
-    launches_per_step = None
+    launches_per_step = st["kernel_launches"]
     # end to end through the C ABI: host mesh and grid in, every block's CSR out
     e2e = None
     if args.e2e:
@@ -255,7 +254,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "far_kernel (FP32 FMA pipe)",
                          "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x 2070 MHz max clock" % sm_count},
-            "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step,
+            "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
             "fp64_gpu": fp64_cmp, "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -266,7 +265,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="sphere20480", choices=sorted(CONFIGS))

@@ -114,6 +114,7 @@ typedef struct {
     double ms_far;           /* far-field quadrature */
     double ms_near;          /* near-field quadrature */
     double ms_extract;       /* CSR extraction */
+    int64_t kernel_launches; /* kernels launched by the last tdbem_assemble_all */
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */

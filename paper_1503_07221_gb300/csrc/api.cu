@@ -887,6 +887,13 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     A->stats.ms_near = ms[2];
     A->stats.ms_extract = ms[3];
     A->stats.ms_total = ms[0] + ms[1] + ms[2] + ms[3];
+    {
+        // tables 4, bounds + windows + counter 3, row counts 1, scans 2, fills 2,
+        // and per colour: far, near (+ far special blocks in the mixed path)
+        int64_t ncol = 0;
+        for (size_t c = 0; c + 1 < A->color_off.size(); ++c) ncol += A->color_off[c + 1] > A->color_off[c];
+        A->stats.kernel_launches = 12 + ncol * (A->fp64 ? 2 : 3);
+    }
     if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
     A->assembled = true;
     return TDBEM_OK;
