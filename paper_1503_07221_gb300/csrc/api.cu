@@ -178,7 +178,7 @@ struct tdbem_mesh {
     std::vector<std::vector<int32_t>> colors;
     std::vector<int32_t> chunk_vptr, chunk_vert, chunk_sptr, chunk_src;
     int64_t nchunks = 0;
-    double diam = 0.0, max_dq = 0.0, max_star = 0.0;
+    double diam = 0.0, max_dq = 0.0, max_star = 0.0, coord_scale = 0.0;
     double rule_L[7][3], rule_W[7];
 };
 
@@ -337,6 +337,7 @@ static tdbem_status build_mesh(tdbem_mesh &m) {
             if (v > dm) dm = v;
         }
     m.diam = sqrt(dm);
+    for (int64_t i = 0; i < 3 * M; ++i) m.coord_scale = std::max(m.coord_scale, fabs(V[i]));
     for (int64_t v = 0; v < M; ++v) {
         std::vector<int32_t> pts;
         for (int64_t x = m.vt_ptr[v]; x < m.vt_ptr[v + 1]; ++x)
@@ -706,6 +707,9 @@ static LagTables make_lt(tdbem_asm *A) {
     lt.dt = A->tg->dt;
     lt.inv_dt = 1.0 / A->tg->dt;
     lt.tie = 1e-12 * A->tg->T;
+    // FP32 squared distances of points with |coordinate| <= L carry an absolute
+    // error of a few ulp(L^2); take 64 ulps of 4 L^2 as the band
+    lt.tol2 = 64.0 * 4.0 * A->mesh->coord_scale * A->mesh->coord_scale * 1.1920928955078125e-07;
     return lt;
 }
 

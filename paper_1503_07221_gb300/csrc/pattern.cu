@@ -16,61 +16,12 @@ __device__ static inline d3 add(d3 a, d3 b) { return {a.x + b.x, a.y + b.y, a.z 
 __device__ static inline d3 mul(d3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
 __device__ static inline double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// Squared distance from p to triangle (a,b,c): the closest point lies in one
-// of the seven Voronoi regions of the triangle (vertices, edges, interior).
-__device__ static double point_triangle_d2(d3 p, d3 a, d3 b, d3 c) {
-    const d3 ab = sub(b, a), ac = sub(c, a), ap = sub(p, a);
-    const double d1 = dot(ab, ap), d2 = dot(ac, ap);
-    if (d1 <= 0.0 && d2 <= 0.0) return dot(ap, ap);
-    const d3 bp = sub(p, b);
-    const double d3_ = dot(ab, bp), d4 = dot(ac, bp);
-    if (d3_ >= 0.0 && d4 <= d3_) return dot(bp, bp);
-    const double vc = d1 * d4 - d3_ * d2;
-    if (vc <= 0.0 && d1 >= 0.0 && d3_ <= 0.0) {
-        const d3 q = add(a, mul(ab, d1 / (d1 - d3_)));
-        const d3 e = sub(p, q);
-        return dot(e, e);
-    }
-    const d3 cp = sub(p, c);
-    const double d5 = dot(ab, cp), d6 = dot(ac, cp);
-    if (d6 >= 0.0 && d5 <= d6) return dot(cp, cp);
-    const double vb = d5 * d2 - d1 * d6;
-    if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
-        const d3 q = add(a, mul(ac, d2 / (d2 - d6)));
-        const d3 e = sub(p, q);
-        return dot(e, e);
-    }
-    const double va = d3_ * d6 - d5 * d4;
-    if (va <= 0.0 && (d4 - d3_) >= 0.0 && (d5 - d6) >= 0.0) {
-        const d3 q = add(b, mul(sub(c, b), (d4 - d3_) / ((d4 - d3_) + (d5 - d6))));
-        const d3 e = sub(p, q);
-        return dot(e, e);
-    }
-    const double den = 1.0 / (va + vb + vc);
-    const d3 q = add(a, add(mul(ab, vb * den), mul(ac, vc * den)));
-    const d3 e = sub(p, q);
-    return dot(e, e);
-}
-
 __device__ static inline double clamp01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
 
-// Squared distance between segments p0 + s (p1 - p0) and q0 + u (q1 - q0),
-// s, u in [0,1]: minimise over the square, clamping the unconstrained
-// minimiser and re-solving for the other parameter.
-__device__ static double segment_segment_d2(d3 p0, d3 p1, d3 q0, d3 q1) {
-    const d3 d1 = sub(p1, p0), d2 = sub(q1, q0), r = sub(p0, q0);
-    const double a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
-    double s, u;
-    const double c = dot(d1, r), b = dot(d1, d2);
-    const double den = a * e - b * b;
-    s = den > 0.0 ? clamp01((b * f - c * e) / den) : 0.0;
-    u = (b * s + f) / e;
-    if (u < 0.0) { u = 0.0; s = clamp01(-c / a); }
-    else if (u > 1.0) { u = 1.0; s = clamp01((b - c) / a); }
-    const d3 w = sub(add(p0, mul(d1, s)), add(q0, mul(d2, u)));
-    return dot(w, w);
-}
-
+// The squared distance of a point to a triangle uses the seven Voronoi
+// regions of the triangle (vertices, edges, interior); that of two segments
+// minimises over [0,1]^2 by clamping the unconstrained minimiser and
+// re-solving for the other parameter. Both are templated on the precision.
 // ----------------------------------------------------------- bounds pass
 // Lowest lag in [lo, hi] with b_d > x (b increasing in d); hi + 1 if none.
 __device__ static int first_b_above(const double *b, int lo, int hi, double x) {
@@ -91,37 +42,84 @@ __device__ static int last_a_below(const double *a, int lo, int hi, double x) {
     return L;
 }
 
-__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // trial
-    const int64_t q = blockIdx.y;                                       // test
-    if (s >= g.E) return;
-    const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
-    int shared = 0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) shared += (A[i] == B[j]);
-    d3 a[3], b[3];
-    for (int i = 0; i < 3; ++i) { a[i] = ld3(g.V + 3 * A[i]); b[i] = ld3(g.V + 3 * B[i]); }
-    double mx = 0.0;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) { const d3 d = sub(a[i], b[j]); mx = fmax(mx, dot(d, d)); }
-    const double dmax = sqrt(mx);
-    double dmin = 0.0;
-    if (!shared) {
-        double m2 = 1e300;
-        for (int i = 0; i < 3; ++i) {
-            m2 = fmin(m2, point_triangle_d2(a[i], b[0], b[1], b[2]));
-            m2 = fmin(m2, point_triangle_d2(b[i], a[0], a[1], a[2]));
-        }
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j)
-                m2 = fmin(m2, segment_segment_d2(a[i], a[(i + 1) % 3], b[j], b[(j + 1) % 3]));
-        dmin = sqrt(m2);
+// FP32 copies of the geometry helpers for the prefilter
+struct f3 { float x, y, z; };
+__device__ static inline f3 sub(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ static inline f3 add(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ static inline f3 mul(f3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ static inline float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ static inline float clamp01(float x) { return x < 0.f ? 0.f : (x > 1.f ? 1.f : x); }
+
+template <typename V, typename T>
+__device__ static T point_triangle_d2t(V p, V a, V b, V c) {
+    const V ab = sub(b, a), ac = sub(c, a), ap = sub(p, a);
+    const T d1 = dot(ab, ap), d2 = dot(ac, ap);
+    if (d1 <= T(0) && d2 <= T(0)) return dot(ap, ap);
+    const V bp = sub(p, b);
+    const T d3_ = dot(ab, bp), d4 = dot(ac, bp);
+    if (d3_ >= T(0) && d4 <= d3_) return dot(bp, bp);
+    const T vc = d1 * d4 - d3_ * d2;
+    if (vc <= T(0) && d1 >= T(0) && d3_ <= T(0)) {
+        const V e = sub(p, add(a, mul(ab, d1 / (d1 - d3_))));
+        return dot(e, e);
     }
-    PairRec r;
+    const V cp = sub(p, c);
+    const T d5 = dot(ab, cp), d6 = dot(ac, cp);
+    if (d6 >= T(0) && d5 <= d6) return dot(cp, cp);
+    const T vb = d5 * d2 - d1 * d6;
+    if (vb <= T(0) && d2 >= T(0) && d6 <= T(0)) {
+        const V e = sub(p, add(a, mul(ac, d2 / (d2 - d6))));
+        return dot(e, e);
+    }
+    const T va = d3_ * d6 - d5 * d4;
+    if (va <= T(0) && (d4 - d3_) >= T(0) && (d5 - d6) >= T(0)) {
+        const V e = sub(p, add(b, mul(sub(c, b), (d4 - d3_) / ((d4 - d3_) + (d5 - d6)))));
+        return dot(e, e);
+    }
+    const T den = T(1) / (va + vb + vc);
+    const V e = sub(p, add(a, add(mul(ab, vb * den), mul(ac, vc * den))));
+    return dot(e, e);
+}
+
+template <typename V, typename T>
+__device__ static T segment_segment_d2t(V p0, V p1, V q0, V q1) {
+    const V d1 = sub(p1, p0), d2 = sub(q1, q0), r = sub(p0, q0);
+    const T a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+    const T c = dot(d1, r), b = dot(d1, d2);
+    const T den = a * e - b * b;
+    T s = den > T(0) ? clamp01((b * f - c * e) / den) : T(0);
+    T u = (b * s + f) / e;
+    if (u < T(0)) { u = T(0); s = clamp01(-c / a); }
+    else if (u > T(1)) { u = T(1); s = clamp01((b - c) / a); }
+    const V w = sub(add(p0, mul(d1, s)), add(q0, mul(d2, u)));
+    return dot(w, w);
+}
+
+// squared minimum and maximum distance of two triangles (dmin = 0 when
+// they share a vertex: closed surfaces, touching triangles never intersect)
+template <typename V, typename T>
+__device__ static void tri_bounds2(const V *a, const V *b, bool shared, T &dmin2, T &dmax2) {
+    T mx = T(0);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { const V d = sub(a[i], b[j]); mx = fmax(mx, dot(d, d)); }
+    dmax2 = mx;
+    if (shared) { dmin2 = T(0); return; }
+    T m2 = T(1e30);
+    for (int i = 0; i < 3; ++i) {
+        m2 = fmin(m2, point_triangle_d2t<V, T>(a[i], b[0], b[1], b[2]));
+        m2 = fmin(m2, point_triangle_d2t<V, T>(b[i], a[0], a[1], a[2]));
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) m2 = fmin(m2, segment_segment_d2t<V, T>(a[i], a[(i + 1) % 3], b[j], b[(j + 1) % 3]));
+    dmin2 = m2;
+}
+
+// Kept lag range of each lag class and kept special blocks from distance
+// bounds (exact FP64 decisions: dmin < b_d - tie, dmax > a_d + tie).
+__device__ static void decide(const LagTables &lt, double dmin, double dmax, PairRec &r) {
     for (int c = 0; c < NLAG; ++c) {
         r.lo[c] = 0; r.cnt[c] = 0;
         if (lt.dlo[c] > lt.dhi[c]) continue;
-        // kept iff dmin < b_d - tie and dmax > a_d + tie (open support, ties cull)
         const int lo = first_b_above(lt.b[c], lt.dlo[c], lt.dhi[c], dmin + lt.tie);
         const int hi = last_a_below(lt.a[c], lt.dlo[c], lt.dhi[c], dmax - lt.tie);
         if (lo <= hi) { r.lo[c] = (int16_t)lo; r.cnt[c] = (uint8_t)(hi - lo + 1); }
@@ -132,6 +130,44 @@ __global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
         if (dmin < lt.b[c][0] - lt.tie && dmax > lt.a[c][0] + lt.tie) sm |= (uint8_t)(1u << (c - NLAG));
     }
     r.smask = sm;
+}
+
+// One thread per element pair. The bounds are first computed in FP32; the
+// lag decisions are taken at both ends of a band of +-tol2 around the FP32
+// squared distances (tol2 covers the FP32 rounding of the squared distances
+// with a wide margin) and, only when the two ends disagree, the pair is
+// recomputed exactly in FP64. The decisions are therefore those of the FP64
+// computation.
+__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // trial
+    const int64_t q = blockIdx.y;                                       // test
+    if (s >= g.E) return;
+    const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
+    int shared = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) shared += (A[i] == B[j]);
+    f3 a[3], b[3];
+    for (int i = 0; i < 3; ++i) {
+        const double *pa = g.V + 3 * A[i], *pb = g.V + 3 * B[i];
+        a[i] = {(float)pa[0], (float)pa[1], (float)pa[2]};
+        b[i] = {(float)pb[0], (float)pb[1], (float)pb[2]};
+    }
+    float mn2, mx2;
+    tri_bounds2<f3, float>(a, b, shared != 0, mn2, mx2);
+    PairRec r0, r1;
+    const double t2 = lt.tol2;
+    decide(lt, shared ? 0.0 : sqrt(fmax((double)mn2 - t2, 0.0)), sqrt(fmax((double)mx2 - t2, 0.0)), r0);
+    decide(lt, shared ? 0.0 : sqrt((double)mn2 + t2), sqrt((double)mx2 + t2), r1);
+    bool same = r0.smask == r1.smask;
+    for (int c = 0; c < NLAG; ++c) same = same && r0.lo[c] == r1.lo[c] && r0.cnt[c] == r1.cnt[c];
+    PairRec r = r0;
+    if (!same) {
+        d3 ad[3], bd[3];
+        for (int i = 0; i < 3; ++i) { ad[i] = ld3(g.V + 3 * A[i]); bd[i] = ld3(g.V + 3 * B[i]); }
+        double dn2, dx2;
+        tri_bounds2<d3, double>(ad, bd, shared != 0, dn2, dx2);
+        decide(lt, sqrt(dn2), sqrt(dx2), r);
+    }
     r.adj = (uint8_t)shared;
     for (int k = 0; k < 5; ++k) r.pad[k] = 0;
     rec[q * g.E + s] = r;

@@ -89,6 +89,7 @@ struct LagTables {
     int rho[NCLASS], P[NCLASS];
     double dt, inv_dt;
     double tie;  // support endpoints: bounds within tie of an endpoint count as equal (culled)
+    double tol2; // band around FP32 squared distances inside which the FP64 bounds decide
 };
 
 // FP32 Chebyshev coefficients of all 16 panels (one sub-panel per unit),
