@@ -21,11 +21,15 @@ __device__ static inline double dsum_warp(double v) {
     return v;
 }
 
+constexpr int NEAR_CELLS = 16;  // lag cells floor(r/dt) a near point pair can occupy
+
 __global__ void __launch_bounds__(NEAR_THREADS)
 near_kernel(const NearArgs A) {
-    extern __shared__ __align__(16) double sm[];  // npp x 6: r, w/r, lx0, lx1, ly0, ly1
+    extern __shared__ __align__(16) double sm[];  // npp x 6: r, w/r, lx0, lx1, ly0, ly1; then npp x int16 order
     __shared__ int items[64];
     __shared__ int nitems;
+    __shared__ int bstart[NEAR_CELLS + 1];
+    __shared__ int wcnt[NEAR_WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Geo &g = A.g;
     const int64_t M = g.M, E = g.E, MM = M * M;
@@ -66,6 +70,33 @@ near_kernel(const NearArgs A) {
                 q[2] = 1.0 - xh0; q[3] = xh0 - xh1;
                 q[4] = 1.0 - yh0; q[5] = yh0 - yh1;
             }
+            __syncthreads();
+            // stable counting sort of the point pairs by lag cell: a block's
+            // support is then one contiguous run of the order (no idle lanes)
+            int16_t *order = reinterpret_cast<int16_t *>(sm + 6 * npp);
+            {
+                int base = 0;
+                for (int cb = 0; cb < NEAR_CELLS; ++cb) {
+                    if (threadIdx.x == 0) bstart[cb] = base;
+                    for (int p0 = 0; p0 < npp; p0 += NEAR_THREADS) {
+                        const int p = p0 + threadIdx.x;
+                        int cl = NEAR_CELLS;
+                        if (p < npp) cl = min((int)floor(sm[6 * p] * inv_dt), NEAR_CELLS - 1);
+                        const bool in = cl == cb;
+                        const unsigned bal = __ballot_sync(0xffffffffu, in);
+                        if (lane == 0) wcnt[w] = __popc(bal);
+                        __syncthreads();
+                        int off = base;
+                        for (int k = 0; k < w; ++k) off += wcnt[k];
+                        if (in) order[off + __popc(bal & ((1u << lane) - 1u))] = (int16_t)p;
+                        int tot = 0;
+                        for (int k = 0; k < NEAR_WARPS; ++k) tot += wcnt[k];
+                        __syncthreads();
+                        base += tot;
+                    }
+                }
+                if (threadIdx.x == 0) bstart[NEAR_CELLS] = base;
+            }
             if (threadIdx.x == 0) {
                 const PairRec rc = A.rec[tau * E + sg];
                 int n = 0;
@@ -86,7 +117,11 @@ near_kernel(const NearArgs A) {
                 int p0 = 0;
                 for (int x = 0; x < c; ++x) p0 += A.lt.P[x];
                 double Sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, St = 0.0;
-                for (int p = lane; p < npp; p += 32) {
+                // cells d + rho .. d + rho + P - 1 hold this block's support
+                const int c0 = max(d + rho, 0), c1 = min(d + rho + P, NEAR_CELLS);
+                const int k0 = c0 < c1 ? bstart[c0] : 0, k1 = c0 < c1 ? bstart[c1] : 0;
+                for (int kk = k0 + lane; kk < k1; kk += 32) {
+                    const int p = order[kk];
                     const double *q = sm + 6 * p;
                     const double v = q[0] * inv_dt - (double)d - (double)rho;
                     if (!(v >= 0.0 && v < (double)P)) continue;
@@ -253,7 +288,7 @@ void launch_farspec(const NearArgs &a, int grid, cudaStream_t st) {
 void launch_near(const NearArgs &a, int grid, cudaStream_t st) {
     int mx = 0;
     for (int k = 1; k <= 3; ++k) mx = a.ss_npp[k] > mx ? a.ss_npp[k] : mx;
-    const size_t smem = (size_t)mx * 6 * sizeof(double);
+    const size_t smem = (size_t)mx * 6 * sizeof(double) + (size_t)mx * sizeof(int16_t) + 16;
     cudaFuncSetAttribute(near_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     near_kernel<<<grid, NEAR_THREADS, smem, st>>>(a);
 }
