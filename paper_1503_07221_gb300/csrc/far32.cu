@@ -2,15 +2,20 @@
 // pair anchor), element pairs without a shared vertex, 7-point rule on both
 // triangles (Eq. MatrixEntries).
 //
-// CTA = 14 warps over 32 trial triangles sigma (lanes) and the 7 test points
-// x_w of the test triangle tau: warps 0..6 evaluate psi for test point w and
-// keep t_b = sum_y w_y lambda_b(y) psi / r (b = 0, 1, 2) per lag slot; warps
-// 7..13 evaluate psi~ for test point w - 7 and keep s~ = sum_y w_y psi~ / r.
-// Both halves share the retarded argument: on an equidistant grid every
-// block class sees q = r / dt in one unit cell, so one Chebyshev argument
+// CTA = 7 compute warps over 32 trial triangles sigma (lanes) and the 7 test
+// points x_w of the test triangle tau (warp w), plus one producer warp that
+// prepares the next chunk's FP64 setup in a second buffer.
+//
+// Every block class shares the retarded argument: on an equidistant grid all
+// classes see q = r / dt in one unit cell, so one Chebyshev argument
 // u = frac(q) serves every panel of every class and only the lag a panel
-// feeds depends on floor(q) (Sec. 3.1, Eq. psiTildeRed); the panel
-// coefficients come from the constant bank, uniform across the warp.
+// feeds depends on floor(q) (Sec. 3.1, Eq. psiTildeRed). A thread evaluates
+// psi and psi~ of a panel together as one packed FP32 pair (fma.rn.f32x2):
+// the coefficients are stored as (psi, psi~) pairs, so one instruction adds a
+// Chebyshev term of both functions, and the distance and T_n are computed
+// once per point pair. It keeps, per lag slot, the pairs
+//   (t_0, t_1) and (t_2, s~),  t_b = sum_y w_y lambda_b(y) psi / r,
+//                              s~  = sum_y w_y psi~ / r.
 //
 // r - R0 = (2 D.e + e.e) / (R0 + r), with D = c_tau - c_sigma and R0 = |D| in
 // FP64 per element pair and e the FP32 difference of the points' offsets
@@ -27,11 +32,34 @@
 namespace tdbem {
 
 constexpr int F32_XW = 7;
-constexpr int F32_WARPS = 2 * F32_XW;
-constexpr int F32_THREADS = F32_WARPS * 32;
-constexpr int F32_THREADS_ALL = F32_THREADS + 32;  // + one producer warp
+constexpr int F32_THREADS_ALL = (F32_XW + 1) * 32;
+
+typedef unsigned long long f2;  // two packed floats (lo, hi)
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// d = a * b + c on both halves, round to nearest
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 coef2(const ChebF32 &C, int p, int n) {
+    return *reinterpret_cast<const f2 *>(&C.c[p][n][0]);
+}
+__device__ __forceinline__ f2 lo2(const ChebF32 &C, int p, int n) {
+    return *reinterpret_cast<const f2 *>(&C.lo[p][n][0]);
+}
 
 struct Setup32 {
+    int64_t tau, ch;
+    int32_t Ft[3];
     float scale[32];
     float nn[32];
     int base[32];
@@ -43,106 +71,87 @@ struct Setup32 {
     float curl[32][9];
 };
 
-// Chebyshev sums of NP consecutive panels (psi: COMP 0, psi~: COMP 1) at
-// argument x. The terms n >= NLOW (at most a few 1e-3 of the panel maximum)
-// are summed forward while the T_n recurrence runs; then the FP32 residuals
-// of the leading coefficients and the terms n < NLOW are added from n =
-// NLOW-1 down to 0 from the kept T_n. Small terms therefore enter before the
-// large leading ones, and the rounding of the leading coefficients does not
-// become a fixed perturbation of psi, which the quadrature would not average
-// away and the cancellation in the odd prototype would amplify.
+// (psi, psi~) of the ten lag-class panels (C1: 3, C2: 4, C3: 3) at argument
+// x, sharing one T_n recurrence. The terms n >= NLOW (at most a few 1e-3 of
+// the panel maximum) are summed forward while the recurrence runs; then the
+// FP32 residuals of the leading coefficients and the terms n < NLOW are added
+// from n = NLOW-1 down to 0 from the kept T_n. Small terms therefore enter
+// before the large leading ones, and the rounding of the leading coefficients
+// does not become a fixed perturbation of psi, which the quadrature would not
+// average away and the cancellation in the odd prototype would amplify.
 constexpr int NLOW = 8;
-template <int NP, int COMP>
-__device__ __forceinline__ void panel_values(const ChebF32 &C, int p0, float x, float *out) {
-    float T[NLOW];
-    T[0] = 1.f;
-    T[1] = x;
+__device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10]) {
+    f2 T[NLOW];
+    float t0 = 1.f, t1 = x;
     const float x2 = x + x;
+    T[0] = pk(1.f, 1.f);
+    T[1] = pk(x, x);
 #pragma unroll
-    for (int n = 2; n < NLOW; ++n) T[n] = x2 * T[n - 1] - T[n - 2];
-    float hi[NP];
+    for (int n = 2; n < NLOW; ++n) {
+        const float tn = x2 * t1 - t0;
+        t0 = t1;
+        t1 = tn;
+        T[n] = pk(tn, tn);
+    }
+    f2 hi[10];
 #pragma unroll
-    for (int j = 0; j < NP; ++j) hi[j] = 0.f;
-    float tm = T[NLOW - 2], t = T[NLOW - 1];
+    for (int j = 0; j < 10; ++j) hi[j] = 0ull;
 #pragma unroll
     for (int n = NLOW; n < NCHEB; ++n) {
-        const float tn = x2 * t - tm;
-        tm = t;
-        t = tn;
+        const float tn = x2 * t1 - t0;
+        t0 = t1;
+        t1 = tn;
+        const f2 tt = pk(tn, tn);
 #pragma unroll
-        for (int j = 0; j < NP; ++j) hi[j] += C.c[p0 + j][n][COMP] * tn;
+        for (int j = 0; j < 10; ++j) hi[j] = fma2(coef2(C, j, n), tt, hi[j]);
     }
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        float a = 0.f;
+    for (int j = 0; j < 10; ++j) {
+        f2 a = 0ull;
 #pragma unroll
-        for (int n = 0; n < NCHEB_LO; ++n) a += C.lo[p0 + j][n][COMP] * T[n];
-        a += hi[j];
+        for (int n = 0; n < NCHEB_LO; ++n) a = fma2(lo2(C, j, n), T[n], a);
+        a = fma2(pk(1.f, 1.f), hi[j], a);
 #pragma unroll
-        for (int n = NLOW - 1; n >= 0; --n) a += C.c[p0 + j][n][COMP] * T[n];
-        out[j] = a;
+        for (int n = NLOW - 1; n >= 0; --n) a = fma2(coef2(C, j, n), T[n], a);
+        v[j] = a;
     }
 }
 
-// the ten panels of the three lag classes, sharing one recurrence
-template <int COMP>
-__device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, float *v1, float *v2, float *v3) {
-    float v[10];
-    panel_values<10, COMP>(C, cls_panel0(C1), x, v);  // C1 (3), C2 (4), C3 (3) are panels 0..9
-#pragma unroll
-    for (int j = 0; j < 3; ++j) { v1[j] = v[j]; v3[j] = v[7 + j]; }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v2[j] = v[3 + j];
-}
-
-// Accumulate the P panel values of lag class CL at cell offset K = cell + OFF
-// into slots slot0(CL) + K + P - 1 - j: NV = 3 (t_0, t_1, t_2) or 1 (s~).
-template <int OFF, int NV, int CL, int K>
-__device__ __forceinline__ void acc_lag(float (&acc)[slot0<OFF>(NLAG)][NV], const float *v, const float *f) {
+// Accumulate the P panels of lag class CL at cell offset K = cell + OFF: slot
+// slot0(CL) + K + P - 1 - j gets (t_0, t_1) += psi (F_0, F_1) and
+// (t_2, s~) += (psi, psi~) (F_2, w r^-1), with F_b = w r^-1 lambda_b(y).
+template <int OFF, int CL, int K>
+__device__ __forceinline__ void accp(f2 (&a01)[slot0<OFF>(NLAG)], f2 (&a2s)[slot0<OFF>(NLAG)], const f2 (&v)[10],
+                                     f2 F01, f2 F2W) {
     constexpr int P = cls_P(CL);
+    constexpr int pj = cls_panel0(CL);
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         constexpr int s0 = slot0<OFF>(CL) + K + P - 1;
-#pragma unroll
-        for (int b = 0; b < NV; ++b) acc[s0 - j][b] += v[j] * f[b];
+        float ps, pt;
+        upk(v[pj + j], ps, pt);
+        a01[s0 - j] = fma2(pk(ps, ps), F01, a01[s0 - j]);
+        a2s[s0 - j] = fma2(v[pj + j], F2W, a2s[s0 - j]);
     }
 }
 
-template <int OFF, int NV, int K>
-__device__ __forceinline__ void acc_cell(float (&acc)[slot0<OFF>(NLAG)][NV], const float *v1, const float *v2,
-                                         const float *v3, const float *f) {
-    acc_lag<OFF, NV, C1, K>(acc, v1, f);
-    acc_lag<OFF, NV, C2, K>(acc, v2, f);
-    acc_lag<OFF, NV, C3, K>(acc, v3, f);
+template <int OFF, int K>
+__device__ __forceinline__ void accp_cell(f2 (&a01)[slot0<OFF>(NLAG)], f2 (&a2s)[slot0<OFF>(NLAG)], const f2 (&v)[10],
+                                          f2 F01, f2 F2W) {
+    accp<OFF, C1, K>(a01, a2s, v, F01, F2W);
+    accp<OFF, C2, K>(a01, a2s, v, F01, F2W);
+    accp<OFF, C3, K>(a01, a2s, v, F01, F2W);
 }
 
-template <int OFF, int NV>
-__device__ __forceinline__ void acc_switch32(float (&acc)[slot0<OFF>(NLAG)][NV], int k, const float *v1,
-                                             const float *v2, const float *v3, const float *f) {
-    switch (k) {
-        case 0: acc_cell<OFF, NV, 0>(acc, v1, v2, v3, f); break;
-        case 1: acc_cell<OFF, NV, 1>(acc, v1, v2, v3, f); break;
-        case 2: acc_cell<OFF, NV, 2>(acc, v1, v2, v3, f); break;
-        case 3: if constexpr (OFF >= 2) acc_cell<OFF, NV, 3>(acc, v1, v2, v3, f); break;
-        case 4: if constexpr (OFF >= 2) acc_cell<OFF, NV, 4>(acc, v1, v2, v3, f); break;
-        case 5: if constexpr (OFF >= 3) acc_cell<OFF, NV, 5>(acc, v1, v2, v3, f); break;
-        case 6: if constexpr (OFF >= 3) acc_cell<OFF, NV, 6>(acc, v1, v2, v3, f); break;
-        default: break;
-    }
-}
-
-// One warp role: COMP 0 (psi, NV = 3) or 1 (psi~, NV = 1). Writes its
-// accumulators to red[xw][lane][slot][4] at components [COMP ? 3 : 0, ...).
-template <int OFF, int COMP>
-__device__ __forceinline__ void quad_role(const FarArgs &A, const ChebF32 &C, const Setup32 &su, int xw, int lane,
-                                          float dx0, float dx1, float dx2, float *red) {
+// Quadrature of one (test point x_w, trial triangle = lane) pair over the 7
+// trial points; writes red[xw][lane][slot][0..3] = (t_0, t_1, t_2, s~).
+template <int OFF>
+__device__ __forceinline__ void quad_packed(const FarArgs &A, const ChebF32 &C, const Setup32 &su, int xw, int lane,
+                                            float dx0, float dx1, float dx2, float *red) {
     constexpr int NS = slot0<OFF>(NLAG);
-    constexpr int NV = COMP == 0 ? 3 : 1;
-    float acc[NS][NV];
+    f2 a01[NS], a2s[NS];
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-        for (int b = 0; b < NV; ++b) acc[s][b] = 0.f;
+    for (int s = 0; s < NS; ++s) { a01[s] = 0ull; a2s[s] = 0ull; }
     const int valid = su.valid[lane];
     const float f0 = su.f0[lane], R0 = su.R0[lane];
     const float D0 = su.D[lane][0], D1 = su.D[lane][1], D2 = su.D[lane][2];
@@ -161,25 +170,28 @@ __device__ __forceinline__ void quad_role(const FarArgs &A, const ChebF32 &C, co
         const float u = q - cf;
         const float x = u + u - 1.f;
         const float wr = valid ? A.rw32[y] * ir : 0.f;
-        float f[NV];
-        if constexpr (COMP == 0) {
-            f[0] = wr * A.rl32[3 * y]; f[1] = wr * A.rl32[3 * y + 1]; f[2] = wr * A.rl32[3 * y + 2];
-        } else {
-            f[0] = wr;
-        }
+        const f2 F01 = pk(wr * A.rl32[3 * y], wr * A.rl32[3 * y + 1]);
+        const f2 F2W = pk(wr * A.rl32[3 * y + 2], wr);
         if (cell < -OFF || cell > OFF) {
             if (valid) A.status[0] = ST_OFF_RANGE;
             cell = 0;
         }
-        float v1[3], v2[4], v3[3];
-        lag_panels<COMP>(C, x, v1, v2, v3);
-        acc_switch32<OFF, NV>(acc, cell + OFF, v1, v2, v3, f);
+        f2 v[10];
+        lag_panels(C, x, v);
+        switch (cell + OFF) {
+            case 0: accp_cell<OFF, 0>(a01, a2s, v, F01, F2W); break;
+            case 1: accp_cell<OFF, 1>(a01, a2s, v, F01, F2W); break;
+            case 2: accp_cell<OFF, 2>(a01, a2s, v, F01, F2W); break;
+            case 3: if constexpr (OFF >= 2) accp_cell<OFF, 3>(a01, a2s, v, F01, F2W); break;
+            case 4: if constexpr (OFF >= 2) accp_cell<OFF, 4>(a01, a2s, v, F01, F2W); break;
+            case 5: if constexpr (OFF >= 3) accp_cell<OFF, 5>(a01, a2s, v, F01, F2W); break;
+            case 6: if constexpr (OFF >= 3) accp_cell<OFF, 6>(a01, a2s, v, F01, F2W); break;
+            default: break;
+        }
     }
-    float *rp = red + ((size_t)(xw * 32 + lane) * NS) * 4 + (COMP == 0 ? 0 : 3);
+    f2 *rp = reinterpret_cast<f2 *>(red + ((size_t)(xw * 32 + lane) * NS) * 4);
 #pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-        for (int b = 0; b < NV; ++b) rp[4 * s + b] = acc[s][b];
+    for (int s = 0; s < NS; ++s) { rp[2 * s] = a01[s]; rp[2 * s + 1] = a2s[s]; }
 }
 
 // Element-pair setup of one chunk (32 trial triangles) for test triangle tau:
@@ -218,13 +230,11 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
     su.valid[lane] = valid; su.base[lane] = base; su.f0[lane] = f0; su.R0[lane] = R0;
     su.D[lane][0] = D0; su.D[lane][1] = D1; su.D[lane][2] = D2;
     su.scale[lane] = scale; su.nn[lane] = nn;
+    if (lane == 0) { su.tau = tau; su.ch = ch; su.Ft[0] = Ft0; su.Ft[1] = Ft1; su.Ft[2] = Ft2; }
 }
 
 // Special blocks (cell 0 and the first/last-row corner) are not evaluated
 // here: the few far pairs that reach them go through the FP64 pass in near.cu.
-// Warps 0..13 compute (two roles x seven test points); warp 14 prepares the
-// next chunk's setup in the other buffer while they do, so the FP64 setup
-// and its loads stay off the critical path.
 template <int OFF>
 __global__ void __launch_bounds__(F32_THREADS_ALL, 1)
 far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
@@ -234,43 +244,34 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
     float *red = reinterpret_cast<float *>(smem_raw + ((2 * sizeof(Setup32) + 15) / 16) * 16);  // [7][32][NS][4]
     float *Lb = red + (size_t)F32_XW * 32 * NS * 4;                                             // [32][NS][9]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = w == F32_WARPS;
-    const int role = w / F32_XW, xw = w % F32_XW;
+    const bool producer = w == F32_XW;
+    const int xw = w;
     const Geo &g = A.g;
     const int64_t nch = A.nchunks;
-    // flattened sequence of (tau, chunk) items of this CTA
     const int64_t ntau = A.ncolor > blockIdx.x ? (A.ncolor - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t nit = ntau * nch;
     if (nit == 0) return;
     if (producer) chunk_setup(A, A.color_tris[blockIdx.x], 0, lane, sub[0]);
     __syncthreads();
     int64_t cur_tau = -1;
-    int32_t Ft0 = 0, Ft1 = 0, Ft2 = 0;
     float dx0 = 0.f, dx1 = 0.f, dx2 = 0.f;
     for (int64_t it = 0; it < nit; ++it) {
-        const int64_t tix = it / nch, ch = it % nch;
-        const int64_t tau = A.color_tris[blockIdx.x + tix * gridDim.x];
         Setup32 &su = sub[it & 1];
-        if (tau != cur_tau) {
-            cur_tau = tau;
-            Ft0 = g.F[3 * tau]; Ft1 = g.F[3 * tau + 1]; Ft2 = g.F[3 * tau + 2];
-            if (!producer) {
-                dx0 = g.dq32[(tau * 7 + xw) * 3 + 0];
-                dx1 = g.dq32[(tau * 7 + xw) * 3 + 1];
-                dx2 = g.dq32[(tau * 7 + xw) * 3 + 2];
-            }
-        }
         if (producer) {
             if (it + 1 < nit) {
                 const int64_t t2 = A.color_tris[blockIdx.x + ((it + 1) / nch) * gridDim.x];
                 chunk_setup(A, t2, (it + 1) % nch, lane, sub[(it + 1) & 1]);
             }
         } else {
-            if (role == 0) quad_role<OFF, 0>(A, C, su, xw, lane, dx0, dx1, dx2, red);
-            else quad_role<OFF, 1>(A, C, su, xw, lane, dx0, dx1, dx2, red);
+            if (su.tau != cur_tau) {
+                cur_tau = su.tau;
+                dx0 = g.dq32[(cur_tau * 7 + xw) * 3 + 0];
+                dx1 = g.dq32[(cur_tau * 7 + xw) * 3 + 1];
+                dx2 = g.dq32[(cur_tau * 7 + xw) * 3 + 2];
+            }
+            quad_packed<OFF>(A, C, su, xw, lane, dx0, dx1, dx2, red);
         }
         __syncthreads();
-        // ---- sum over the 7 test points -> local 3x3 per (sigma, slot)
         for (int k = threadIdx.x; k < 32 * NS; k += F32_THREADS_ALL) {
             const int sl = k / NS, s = k % NS;
             float Sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, St = 0.f;
@@ -286,7 +287,7 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
                 }
                 St += wx * q[3];
             }
-            const float *gt = g.geo32 + 16 * tau + 4, *gs = su.curl[sl];
+            const float *gt = g.geo32 + 16 * su.tau + 4, *gs = su.curl[sl];
             const float sc = su.scale[sl], nn = su.nn[sl];
             float *lp = Lb + ((size_t)sl * NS + s) * 9;
 #pragma unroll
@@ -298,7 +299,7 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
                 }
         }
         __syncthreads();
-        scatter_chunk<float, OFF, F32_THREADS_ALL, Setup32, false>(A, ch, Ft0, Ft1, Ft2, su, Lb);
+        scatter_chunk<float, OFF, F32_THREADS_ALL, Setup32, false>(A, su.ch, su.Ft[0], su.Ft[1], su.Ft[2], su, Lb);
         __syncthreads();
     }
 }

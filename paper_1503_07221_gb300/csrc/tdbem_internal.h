@@ -95,7 +95,7 @@ struct LagTables {
 // FP32 Chebyshev coefficients of all 16 panels (one sub-panel per unit),
 // passed by value so kernels read them from the constant bank.
 constexpr int NCHEB_LO = 4;  // leading coefficients carried as a hi + lo float pair
-struct ChebF32 {
+struct alignas(8) ChebF32 {  // 8-aligned: read as packed pairs
     float c[TOTAL_PANELS][NCHEB][2];      // (psi, psi~), rounded to FP32
     float lo[TOTAL_PANELS][NCHEB_LO][2];  // c - (double)(float)c of the leading ones
 };
