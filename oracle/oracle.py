@@ -104,6 +104,7 @@ class Oracle:
         self.F = np.ascontiguousarray(tris, dtype=np.int32)
         self.t = np.ascontiguousarray(t, dtype=np.float64)
         self.p = p
+        self.equidistant = bool(equidistant)
         mode = {"direct": 0, "interp": 1}[psi_mode]
         self.h = lib().or_create(self.V, self.V.shape[0], self.F, self.F.shape[0], self.t, self.t.shape[0],
                                  p, int(equidistant), gl_n, gl_sub, ss_n, mode, interp_S, interp_n)
@@ -210,6 +211,52 @@ class Oracle:
                 lst.append((cols[a:e].copy(), vf[a:e].copy(), vn[a:e].copy()))
             out[int(b)] = lst
         return out
+
+    def block_source(self, kb, ib):
+        """Listed block that holds block (kb, ib) of the whole matrix
+        (0-based time indices, Eq. Apartitioned), or None for a zero block.
+
+        Without the equidistant reduction every nonzero block is listed. On an
+        equidistant grid the list holds the first two block columns, the last
+        block row and the blocks (1, 2) and (N-2, N-1); every other block with
+        both indices in the inner range 1..N-2 is, by Eq. relationAtildeBlock,
+        block (k - i + 1, 1) when k >= i and block (1, 2) when k = i - 1, and
+        is zero above that (Hessenberg, Eq. Apartitioned). Blocks cut by the
+        diam criterion (Sec. 5.1) are absent from the list and zero."""
+        if not hasattr(self, "_bidx"):
+            self._bidx = {(b[0], b[1]): n for n, b in enumerate(self.blocks())}
+        N = self.N
+        key = (kb, ib)
+        if self.equidistant and 1 <= kb <= N - 2 and 1 <= ib <= N - 2:
+            d = kb - ib
+            if d >= 0:
+                key = (d + 1, 1)
+            elif d == -1:
+                key = (1, 2)
+            else:
+                return None
+        return self._bidx.get(key)
+
+    def hessenberg_apply(self, x, rows=None):
+        """y = A x for the whole space-time system (Eq. Apartitioned): x and y
+        are (N, M) arrays, x[i] the coefficients of trial time basis function
+        i, y[k] the result on test function k. With `rows` given, only the
+        columns y[:, rows] are computed (the rest stay zero). Every block
+        comes from the listed blocks through block_source."""
+        x = np.asarray(x, dtype=np.float64)
+        N, M = self.N, self.M
+        rows = np.arange(M) if rows is None else np.asarray(rows, dtype=np.int64)
+        nb = self.num_blocks()
+        R = self.assemble_rows(rows, np.arange(nb))
+        y = np.zeros((N, M))
+        for kb in range(N):
+            for ib in range(N):
+                b = self.block_source(kb, ib)
+                if b is None:
+                    continue
+                for r, (c, f, n) in enumerate(R[b]):
+                    y[kb, rows[r]] += np.dot(f + n, x[ib, c])
+        return y
 
     def dense_block(self, blk):
         """The whole block as a dense M x M array (far + near), row = test vertex."""
