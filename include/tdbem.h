@@ -176,6 +176,21 @@ TDBEM_API tdbem_status tdbem_block_csr(const tdbem_asm *a, int64_t b, int32_t wh
 TDBEM_API tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32_t which, int64_t *rp,
                                   int32_t *col, void *val);
 
+/* y = A x for the whole block-Hessenberg space-time matrix (Sec. 5.1, Eq.
+ * Apartitioned), every block taken from the unique blocks of the last
+ * assembly through Eq. relationAtildeBlock; blocks cut by the diam criterion
+ * are zero. x and y are caller-owned device arrays of N*M doubles, block row
+ * k at [k*M, k*M + M) (time index k of the trial / test basis function,
+ * vertex index within); they must not overlap. Far values (float in MIXED
+ * mode) are widened to double; products and sums are FP64. Asynchronous on
+ * `stream`; uses a scratch buffer owned by the assembler (N*M doubles,
+ * allocated by tdbem_assemble_all), so calls on one assembler must be
+ * ordered on one stream. TDBEM_E_NOT_ASSEMBLED before an assembly,
+ * TDBEM_E_INVALID_ARG for NULL or overlapping x / y, TDBEM_E_CUDA if the
+ * launch fails. */
+TDBEM_API tdbem_status tdbem_hessenberg_apply(const tdbem_asm *a, const double *x_dev, double *y_dev,
+                                              void *stream);
+
 /* Assembly counters and the per-phase device times of the last assembly. */
 TDBEM_API tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
 

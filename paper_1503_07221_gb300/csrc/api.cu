@@ -391,6 +391,9 @@ struct tdbem_asm {
     bool assembled = false;
     tdbem_stats_t stats{};
     size_t col_far_cap = 0, col_near_cap = 0;
+    // block-Hessenberg matvec: run descriptors and the transposed-x scratch
+    DevBuf mv_blk, mv_xT;
+    std::vector<MvBlock> mv_host;
 };
 
 static int kind_of(int64_t i, int64_t N) { return i == 0 ? 0 : (i == N - 1 ? 2 : 1); }  // F, I, L
@@ -713,6 +716,40 @@ static LagTables make_lt(tdbem_asm *A) {
     return lt;
 }
 
+// Diagonal run of block positions that unique block (k, i) stands for
+// (0-based; Eq. relationAtildeBlock holds for 1 <= k, i <= N-2): the inner
+// blocks of the second block column repeat down their diagonal, block (1, 2)
+// along the superdiagonal, every other listed block is used once.
+static void block_run(int64_t k, int64_t i, int64_t N, int32_t &k0, int32_t &i0, int32_t &cnt) {
+    k0 = (int32_t)k;
+    i0 = (int32_t)i;
+    cnt = 1;
+    if (i == 1 && k >= 1 && k <= N - 2) cnt = (int32_t)(N - 1 - k);
+    else if (k == 1 && i == 2) cnt = (int32_t)(N - 3);
+}
+
+static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
+    const int64_t N = A.tg->N, M = A.mesh->M;
+    const size_t nb = A.blocks.size();
+    A.mv_host.assign(nb, MvBlock{});
+    for (size_t b = 0; b < nb; ++b) {
+        MvBlock &d = A.mv_host[b];
+        d.rp_far = (const int64_t *)A.rp_far.p + b * (M + 1);
+        d.col_far = (const int32_t *)A.col_far.p + A.off_far[b];
+        d.val_far = (const char *)A.val_far.p + A.off_far[b] * (A.fp64 ? 8 : 4);
+        d.rp_near = (const int64_t *)A.rp_near.p + b * (M + 1);
+        d.col_near = (const int32_t *)A.col_near.p + A.off_near[b];
+        d.val_near = (const double *)A.val_near.p + A.off_near[b];
+        block_run(A.blocks[b].kb, A.blocks[b].ib, N, d.k0, d.i0, d.cnt);
+    }
+    tdbem_status s;
+    if ((s = upload(A.mv_blk, A.mv_host, st))) return s;
+    if (A.mv_xT.n < (size_t)(N * M) * sizeof(double))
+        if ((s = dev_alloc(A.mv_xT, (size_t)(N * M) * sizeof(double), st))) return s;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
     cudaStream_t st = (cudaStream_t)stream;
@@ -899,6 +936,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         A->stats.kernel_launches = 12 + ncol * (A->fp64 ? 2 : 3);
     }
     if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
+    if ((s = plan_matvec(*A, st))) return s;
     A->assembled = true;
     return TDBEM_OK;
 }
@@ -938,6 +976,22 @@ tdbem_status tdbem_block_csr_host(const tdbem_asm *A, int64_t b, int32_t which, 
     if (rp) CUDA_TRY(cudaMemcpy(rp, drp, (M + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     if (col && nnz) CUDA_TRY(cudaMemcpy(col, dcol, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
     if (val && nnz) CUDA_TRY(cudaMemcpy(val, dval, nnz * vs, cudaMemcpyDeviceToHost));
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double *y, void *stream) {
+    if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    const int64_t N = A->tg->N, M = A->mesh->M;
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    const size_t bytes = (size_t)(N * M) * sizeof(double);
+    if (xb < yb + bytes && yb < xb + bytes) return fail(TDBEM_E_INVALID_ARG, "x and y overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, (double *)A->mv_xT.p, y,
+                               M, (int)N, nsm, st));
     return TDBEM_OK;
 }
 

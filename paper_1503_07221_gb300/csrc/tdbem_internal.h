@@ -187,4 +187,20 @@ void launch_near(const NearArgs &a, int grid, cudaStream_t st);
 // far element pairs that reach a special block, FP64 7-point rule
 void launch_farspec(const NearArgs &a, int grid, cudaStream_t st);
 
+// matvec.cu: one unique block and the diagonal run of block positions
+// (k0 + p, i0 + p), p < cnt, that it stands for (Eq. relationAtildeBlock)
+struct MvBlock {
+    const int64_t *rp_far;
+    const int32_t *col_far;
+    const void *val_far;  // float (mixed) or double (FP64)
+    const int64_t *rp_near;
+    const int32_t *col_near;
+    const double *val_near;
+    int32_t k0, i0, cnt, pad;
+};
+size_t hessenberg_smem(int N);
+// transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
+cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
+                              int64_t M, int N, int nsm, cudaStream_t st);
+
 }  // namespace tdbem

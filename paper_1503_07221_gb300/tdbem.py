@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdbem.so")
 
 OK = 0
+E_INVALID_ARG, E_MESH, E_TIMEGRID, E_OOM, E_CUDA, E_DEVICE, E_NOT_ASSEMBLED, E_UNSUPPORTED = range(1, 9)
 PREC_FP64 = 0
 PREC_MIXED = 1
 FAR = 0
@@ -65,6 +66,7 @@ def lib():
     L.tdbem_assemble_all.argtypes = [vp, vp]
     L.tdbem_block_csr.argtypes = [vp, i64, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.tdbem_block_csr_host.argtypes = [vp, i64, i32, vp, vp, vp]
+    L.tdbem_hessenberg_apply.argtypes = [vp, vp, vp, vp]
     L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
     L.tdbem_mesh_destroy.argtypes = [vp]
     L.tdbem_timegrid_destroy.argtypes = [vp]
@@ -217,6 +219,21 @@ class Assembler:
         val = np.zeros(max(nnz, 1), vdt)
         _check(lib().tdbem_block_csr_host(self.h, b, which, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
         return rp, col[:nnz], val[:nnz]
+
+    def hessenberg_apply(self, x, y=None, stream=None):
+        """y = A x over the whole block-Hessenberg matrix; x and y are
+        contiguous float64 CUDA tensors of shape (N, M) (row = time index)."""
+        import torch
+        shape = (self.grid.N, self.mesh.M)
+        for name, v in (("x", x), ("y", y)):
+            if v is not None and (tuple(v.shape) != shape or v.dtype != torch.float64 or not v.is_cuda
+                                  or not v.is_contiguous()):
+                raise ValueError("%s must be a contiguous float64 CUDA tensor of shape %s" % (name, shape))
+        if y is None:
+            y = torch.empty_like(x)
+        _check(lib().tdbem_hessenberg_apply(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                            C.c_void_p(_stream(stream))))
+        return y
 
     def stats(self):
         s = Stats()
