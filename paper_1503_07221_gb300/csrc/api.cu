@@ -995,6 +995,26 @@ tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double 
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x, double *y, void *stream) {
+    if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    const int64_t N = A->tg->N, M = A->mesh->M;
+    if (N * M > MV_STATIC_MAX)
+        return fail(TDBEM_E_INVALID_ARG, "N*M = " + std::to_string(N * M) + " exceeds the fixed scratch of " +
+                                             std::to_string(MV_STATIC_MAX) + " doubles");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    const size_t bytes = (size_t)(N * M) * sizeof(double);
+    if (xb < yb + bytes && yb < xb + bytes) return fail(TDBEM_E_INVALID_ARG, "x and y overlap");
+    double *xT = nullptr;
+    CUDA_TRY(static_mv_scratch(&xT));
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, xT, y, M, (int)N,
+                               nsm, (cudaStream_t)stream));
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
     if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = A->stats;

@@ -202,5 +202,9 @@ size_t hessenberg_smem(int N);
 // transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
                               int64_t M, int N, int nsm, cudaStream_t st);
+// noalloc.cu: fixed scratch of MV_STATIC_MAX doubles for the matvec that
+// allocates nothing; its address on the current device
+constexpr int64_t MV_STATIC_MAX = (int64_t)1 << 21;
+cudaError_t static_mv_scratch(double **ptr);
 
 }  // namespace tdbem

@@ -67,6 +67,7 @@ def lib():
     L.tdbem_block_csr.argtypes = [vp, i64, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.tdbem_block_csr_host.argtypes = [vp, i64, i32, vp, vp, vp]
     L.tdbem_hessenberg_apply.argtypes = [vp, vp, vp, vp]
+    L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
     L.tdbem_mesh_destroy.argtypes = [vp]
     L.tdbem_timegrid_destroy.argtypes = [vp]
@@ -220,9 +221,11 @@ class Assembler:
         _check(lib().tdbem_block_csr_host(self.h, b, which, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
         return rp, col[:nnz], val[:nnz]
 
-    def hessenberg_apply(self, x, y=None, stream=None):
+    def hessenberg_apply(self, x, y=None, stream=None, noalloc=False):
         """y = A x over the whole block-Hessenberg matrix; x and y are
-        contiguous float64 CUDA tensors of shape (N, M) (row = time index)."""
+        contiguous float64 CUDA tensors of shape (N, M) (row = time index).
+        noalloc=True calls tdbem_hessenberg_apply_noalloc (fixed scratch,
+        N*M <= 2^21); y must then be given."""
         import torch
         shape = (self.grid.N, self.mesh.M)
         for name, v in (("x", x), ("y", y)):
@@ -230,9 +233,11 @@ class Assembler:
                                   or not v.is_contiguous()):
                 raise ValueError("%s must be a contiguous float64 CUDA tensor of shape %s" % (name, shape))
         if y is None:
+            if noalloc:
+                raise ValueError("noalloc=True needs a caller-provided y")
             y = torch.empty_like(x)
-        _check(lib().tdbem_hessenberg_apply(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
-                                            C.c_void_p(_stream(stream))))
+        fn = lib().tdbem_hessenberg_apply_noalloc if noalloc else lib().tdbem_hessenberg_apply
+        _check(fn(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(_stream(stream))))
         return y
 
     def stats(self):
