@@ -1,8 +1,14 @@
-"""Benchmark: assembly of all unique blocks of the block-Hessenberg system.
+"""Benchmark: assembly of all unique blocks of the block-Hessenberg system,
+then block-Hessenberg matvecs with the assembled matrix.
 
 One step = one tdbem_assemble_all call (psi tables, element-pair bounds,
 vertex-pair windows, far and near quadrature, per-block CSR) on a mesh and
-time grid already resident on the device. Prints one JSON line.
+time grid already resident on the device, followed by --matvecs (default
+20) tdbem_hessenberg_apply calls on seeded N(0,1) vectors already resident
+on the device. value = structural nonzeros assembled per second of the whole
+step. e2e: the same step through the public API from host data: mesh, time
+grid and the right-hand sides copied in (vectors from pinned memory), every
+matvec result copied back to pinned host memory. Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config NAME] [--impl ours|reference]
 
@@ -164,22 +170,41 @@ def run_ours(args):
     mesh, grid = tdbem.Mesh(V, F), tdbem.TimeGrid(t)
     asm = tdbem.Assembler(mesh, grid, precision=prec)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    N, M = t.size, V.shape[0]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1234)
+    X = torch.randn((max(args.matvecs, 1), N, M), dtype=torch.float64, device="cuda", generator=gen)
+    Y = torch.empty((N, M), dtype=torch.float64, device="cuda")
+
+    def step(mv_events=None):
         asm.assemble()
+        if mv_events:
+            mv_events[0].record(stream)
+        for r in range(args.matvecs):
+            asm.hessenberg_apply(X[r], Y)
+        if mv_events:
+            mv_events[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    far_ms = []
+    far_ms, asm_ms, mv_ev = [], [], []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            asm.assemble()
+            e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            step(e)
+            mv_ev.append(e)
             far_ms.append(asm.stats()["ms_far"])
+            asm_ms.append(asm.stats()["ms_total"])
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
+    mv_ms = float(np.mean([a.elapsed_time(b) for a, b in mv_ev])) / max(args.matvecs, 1)
     if dist:
         tm = torch.tensor([ms], device="cuda")
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
@@ -189,25 +214,29 @@ def run_ours(args):
     value = nnz * world / (ms * 1e-3)
     qps = st["quad_points"] * world / (ms * 1e-3)
     nb = st["n_blocks"]
-    launches_per_step = st["kernel_launches"]
-    # end to end through the C ABI: host mesh and grid in, every block's CSR out
+    launches_per_step = st["kernel_launches"] + 2 * args.matvecs  # transpose + product per matvec
+    # end to end through the C ABI: host mesh, grid and right-hand sides in,
+    # assembly, matvecs, every result back to host
     e2e = None
     if args.e2e:
+        Xh = X.cpu().pin_memory()
+        Yh = torch.empty((max(args.matvecs, 1), N, M), dtype=torch.float64).pin_memory()
+        Xd = torch.empty_like(X)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2, g2 = tdbem.Mesh(V, F), tdbem.TimeGrid(t)
         a2 = tdbem.Assembler(m2, g2, precision=prec)
+        Xd.copy_(Xh, non_blocking=True)
         a2.assemble()
-        d2h = 0
-        for b in range(a2.num_blocks()):
-            for which in (tdbem.FAR, tdbem.NEAR):
-                rp, col, val = a2.block_csr_host(b, which)
-                d2h += rp.nbytes + col.nbytes + val.nbytes
+        for r in range(args.matvecs):
+            a2.hessenberg_apply(Xd[r], Y)
+            Yh[r].copy_(Y, non_blocking=True)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         del a2
         e2e = {"value": nnz / (t1 - t0), "unit": "nonzeros/s", "seconds": t1 - t0,
-               "h2d_bytes_per_step": int(V.nbytes + F.nbytes + t.nbytes), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(V.nbytes + F.nbytes + t.nbytes + Xh[:args.matvecs].numel() * 8),
+               "d2h_bytes_per_step": int(Yh[:args.matvecs].numel() * 8)}
     # roofline of the dominant kernel (far field): FP32 FMA pipe
     far_avg_ms = float(np.mean(far_ms))
     flops = far_flops(st)
@@ -217,20 +246,29 @@ def run_ours(args):
     clocks = clk.summary()
     fp64_cmp = None
     if args.fp64_compare and prec == tdbem.PREC_MIXED:
+        y_mixed = asm.hessenberg_apply(X[0]).cpu()
         del asm
         torch.cuda.empty_cache()
         a64 = tdbem.Assembler(mesh, grid, precision=tdbem.PREC_FP64)
         a64.assemble()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         a64.assemble()
         e1.record(stream)
+        for r in range(args.matvecs):
+            a64.hessenberg_apply(X[r], Y)
+        e2.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
+        mv64 = e1.elapsed_time(e2) / max(args.matvecs, 1)
         s64 = a64.stats()
-        fp64_cmp = {"value": s64["nnz"] / (ms64 * 1e-3), "unit": "nonzeros/s", "ms": ms64,
-                    "ms_far": s64["ms_far"], "ms_near": s64["ms_near"]}
+        y64 = a64.hessenberg_apply(X[0]).cpu()
+        rel = float(torch.linalg.norm(y_mixed - y64) / torch.linalg.norm(y64))
+        fp64_cmp = {"value": s64["nnz"] / ((ms64 + args.matvecs * mv64) * 1e-3), "unit": "nonzeros/s",
+                    "ms_step": ms64 + args.matvecs * mv64, "ms_assembly": ms64, "ms_matvec_each": mv64,
+                    "ms_far": s64["ms_far"], "ms_near": s64["ms_near"],
+                    "matvec_rel_diff_mixed_vs_fp64": rel}
         del a64
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -249,7 +287,9 @@ def run_ours(args):
                        "l2": "working set (element-pair records, lag windows, CSR) far larger than L2"},
             "quad_points_per_s": qps,
             "nnz": nnz, "unique_blocks": nb, "quad_points": st["quad_points"],
-            "phase_ms": {k: st[k] for k in ("ms_pattern", "ms_far", "ms_near", "ms_extract")},
+            "phase_ms": dict({k: st[k] for k in ("ms_pattern", "ms_far", "ms_near", "ms_extract")},
+                             ms_assembly=float(np.mean(asm_ms)), ms_matvec_each=mv_ms, matvecs=args.matvecs),
+            "assembly_only_nnz_per_s": nnz * world / (float(np.mean(asm_ms)) * 1e-3),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "far_kernel (FP32 FMA pipe)",
@@ -271,6 +311,7 @@ def main():
     ap.add_argument("--config", default="sphere20480", choices=sorted(CONFIGS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-rows", type=int, default=16)
+    ap.add_argument("--matvecs", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")

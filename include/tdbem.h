@@ -181,8 +181,10 @@ TDBEM_API tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32
  * assembly through Eq. relationAtildeBlock; blocks cut by the diam criterion
  * are zero. x and y are caller-owned device arrays of N*M doubles, block row
  * k at [k*M, k*M + M) (time index k of the trial / test basis function,
- * vertex index within); they must not overlap. Far values (float in MIXED
- * mode) are widened to double; products and sums are FP64. Asynchronous on
+ * vertex index within); they must not overlap. FP64 mode: products and sums
+ * in FP64. MIXED mode: x rounded to FP32, FP32 products of the FP32 far
+ * values summed in FP32 over at most 32 products, partial sums and near
+ * terms accumulated in FP64. Asynchronous on
  * `stream`; uses a scratch buffer owned by the assembler (N*M doubles,
  * allocated by tdbem_assemble_all), so calls on one assembler must be
  * ordered on one stream. TDBEM_E_NOT_ASSEMBLED before an assembly,

@@ -14,9 +14,15 @@
 //   y[k0 + p, l] += sum_j A_b(l, j) xT[j, i0 + p].
 // Runs of 16 or more positions map lanes to positions (broadcast of the
 // nonzero by shuffle); shorter runs map lanes to nonzeros and reduce across
-// the warp. Products and sums are FP64 (far values are widened from FP32 in
-// the mixed path). Every y entry is written by its owning warp only, in a
-// fixed order: the result is deterministic and needs no atomics.
+// the warp. FP64 path: x, products and sums in FP64. Mixed path (FP32 far
+// values): x is rounded to FP32 in the transpose, far products are FP32 and
+// summed in FP32 over at most 32 products, and these partial sums are added
+// in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate on this part); the
+// FP64 near values multiply the same x in FP64. Every y entry is written by
+// its owning warp only, in a fixed order: the result is deterministic and
+// needs no atomics.
+#include <type_traits>
+
 #include "tdbem_internal.h"
 
 namespace tdbem {
@@ -24,20 +30,25 @@ namespace tdbem {
 constexpr int MV_WARPS = 8;
 constexpr int MV_PP = 4;  // positions per lane in one pass of the wide mapping
 
-__global__ void __launch_bounds__(1024) transpose_kernel(const double *__restrict__ x, double *__restrict__ xT,
-                                                         int64_t N, int64_t M) {
+template <typename XT>
+__global__ void __launch_bounds__(1024) transpose_kernel(const double *__restrict__ x, XT *__restrict__ xT, int64_t N,
+                                                         int64_t M) {
     __shared__ double tile[32][33];
     const int64_t j0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
     if (i0 + ty < N && j0 + tx < M) tile[ty][tx] = x[(i0 + ty) * M + j0 + tx];
     __syncthreads();
-    if (j0 + ty < M && i0 + tx < N) xT[(j0 + ty) * N + i0 + tx] = tile[tx][ty];
+    if (j0 + ty < M && i0 + tx < N) xT[(j0 + ty) * N + i0 + tx] = (XT)tile[tx][ty];
 }
 
-template <typename VT>
+// products and sums of one CSR row of one block for the positions of its run.
+// F32: FP32 products of FP32 values and FP32 x, partial sums of at most 32
+// products in FP32, added into FP64; otherwise FP64 products and sums.
+template <typename VT, typename XT, bool F32>
 __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                           const VT *__restrict__ val, int64_t l, int k0, int i0, int cnt,
-                                          const double *__restrict__ xT, int N, double *ys, int lane) {
+                                          const XT *__restrict__ xT, int N, double *ys, int lane) {
+    typedef typename std::conditional<F32, float, double>::type AT;
     const int64_t a = rp[l], e = rp[l + 1];
     if (a == e) return;
     if (cnt >= 16) {
@@ -49,16 +60,21 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
             for (int64_t base = a; base < e; base += 32) {
                 const int n = (int)min((int64_t)32, e - base);
                 int cj = 0;
-                double cv = 0.0;
-                if (lane < n) { cj = col[base + lane]; cv = (double)val[base + lane]; }
+                AT cv = 0;
+                if (lane < n) { cj = col[base + lane]; cv = (AT)val[base + lane]; }
+                AT part[MV_PP];
+#pragma unroll
+                for (int m = 0; m < MV_PP; ++m) part[m] = 0;
                 for (int t = 0; t < n; ++t) {
                     const int j = __shfl_sync(0xffffffffu, cj, t);
-                    const double v = __shfl_sync(0xffffffffu, cv, t);
-                    const double *xr = xT + (int64_t)j * N + i0 + pl;
+                    const AT v = __shfl_sync(0xffffffffu, cv, t);
+                    const XT *xr = xT + (int64_t)j * N + i0 + pl;
 #pragma unroll
                     for (int m = 0; m < MV_PP; ++m)
-                        if (pl + 32 * m < cnt) acc[m] = fma(v, xr[32 * m], acc[m]);
+                        if (pl + 32 * m < cnt) part[m] = fma(v, (AT)xr[32 * m], part[m]);
                 }
+#pragma unroll
+                for (int m = 0; m < MV_PP; ++m) acc[m] += (double)part[m];
             }
 #pragma unroll
             for (int m = 0; m < MV_PP; ++m)
@@ -67,7 +83,13 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
     } else {
         for (int p = 0; p < cnt; ++p) {
             double acc = 0.0;
-            for (int64_t nz = a + lane; nz < e; nz += 32) acc = fma((double)val[nz], xT[(int64_t)col[nz] * N + i0 + p], acc);
+            for (int64_t c0 = a; c0 < e; c0 += 32 * 32) {
+                const int64_t c1 = min(e, c0 + 32 * 32);
+                AT part = 0;
+                for (int64_t nz = c0 + lane; nz < c1; nz += 32)
+                    part = fma((AT)val[nz], (AT)xT[(int64_t)col[nz] * N + i0 + p], part);
+                acc += (double)part;
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) ys[k0 + p] += acc;
@@ -76,10 +98,15 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
     __syncwarp();
 }
 
-template <typename VT>
+// VT: far value type. F32 (mixed path): x in FP32, far products in FP32 with
+// FP64 sums of 32-product partials; the FP64 near values multiply the same
+// FP32 x in FP64. Otherwise (FP64 path) everything is FP64.
+template <typename VT, bool F32>
 __global__ void __launch_bounds__(MV_WARPS * 32) hessenberg_kernel(const MvBlock *__restrict__ blk, int nb,
-                                                                   const double *__restrict__ xT,
+                                                                   const void *__restrict__ xT_,
                                                                    double *__restrict__ y, int64_t M, int N) {
+    typedef typename std::conditional<F32, float, double>::type XT;
+    const XT *xT = (const XT *)xT_;
     extern __shared__ double ys_all[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *ys = ys_all + (size_t)w * N;
@@ -88,8 +115,8 @@ __global__ void __launch_bounds__(MV_WARPS * 32) hessenberg_kernel(const MvBlock
         __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const MvBlock B = blk[b];
-            row_apply<VT>(B.rp_far, B.col_far, (const VT *)B.val_far, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
-            row_apply<double>(B.rp_near, B.col_near, B.val_near, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
+            row_apply<VT, XT, F32>(B.rp_far, B.col_far, (const VT *)B.val_far, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
+            row_apply<double, XT, false>(B.rp_near, B.col_near, B.val_near, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
         }
         for (int k = lane; k < N; k += 32) y[(int64_t)k * M + l] = ys[k];
         __syncwarp();
@@ -98,24 +125,26 @@ __global__ void __launch_bounds__(MV_WARPS * 32) hessenberg_kernel(const MvBlock
 
 size_t hessenberg_smem(int N) { return (size_t)MV_WARPS * N * sizeof(double); }
 
-cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
-                              int64_t M, int N, int nsm, cudaStream_t st) {
+template <typename VT, bool F32>
+static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *xT, double *y, int64_t M, int N,
+                             int nsm, cudaStream_t st) {
+    typedef typename std::conditional<F32, float, double>::type XT;
     const dim3 tg((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
-    transpose_kernel<<<tg, dim3(32, 32), 0, st>>>(x, xT, N, M);
+    transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, N, M);
     const size_t smem = hessenberg_smem(N);
     const int64_t ctas = (M + MV_WARPS - 1) / MV_WARPS;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 8);
-    cudaError_t e;
-    if (far_fp64) {
-        if ((e = cudaFuncSetAttribute(hessenberg_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-            return e;
-        hessenberg_kernel<double><<<grid, MV_WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
-    } else {
-        if ((e = cudaFuncSetAttribute(hessenberg_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
-            return e;
-        hessenberg_kernel<float><<<grid, MV_WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
-    }
+    cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    hessenberg_kernel<VT, F32><<<grid, MV_WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
     return cudaGetLastError();
+}
+
+cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
+                              int64_t M, int N, int nsm, cudaStream_t st) {
+    if (far_fp64) return launch_mv<double, false>(blk, nb, x, xT, y, M, N, nsm, st);
+    return launch_mv<float, true>(blk, nb, x, xT, y, M, N, nsm, st);
 }
 
 }  // namespace tdbem
