@@ -822,7 +822,14 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         fa.cheb64 = (const double *)A->tab_coef4.p;
         for (int k = 0; k < 7; ++k) {
             fa.rw32[k] = (float)m.rule_W[k];
-            for (int d = 0; d < 3; ++d) fa.rl32[3 * k + d] = (float)m.rule_L[k][d];
+            fa.wwh[k] = (float)m.rule_W[k];
+            fa.wwl[k] = (float)(m.rule_W[k] - (double)fa.wwh[k]);
+            for (int d = 0; d < 3; ++d) {
+                fa.rl32[3 * k + d] = (float)m.rule_L[k][d];
+                const double gw = m.rule_W[k] * m.rule_L[k][d];
+                fa.gwh[3 * k + d] = (float)gw;
+                fa.gwl[3 * k + d] = (float)(gw - (double)fa.gwh[3 * k + d]);
+            }
         }
         const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)nsm);
         if (grid > 0) {

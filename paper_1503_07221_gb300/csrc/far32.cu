@@ -50,6 +50,32 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// (h, l) += (gh + gl) t on both halves: exact product error of gh t, two-sum
+// into h, the rest into l
+__device__ __forceinline__ void ff_acc(f2 &h, f2 &l, f2 gh, f2 gl, f2 t) {
+    const f2 p = mul2(gh, t);
+    const f2 pe = fma2(gh, t, sub2(0ull, p));
+    const f2 s = add2(h, p);
+    const f2 bb = sub2(s, h);
+    const f2 e = add2(sub2(h, sub2(s, bb)), sub2(p, bb));
+    l = fma2(gl, t, add2(l, add2(e, pe)));
+    h = s;
+}
 __device__ __forceinline__ f2 coef2(const ChebF32 &C, int p, int n) {
     return *reinterpret_cast<const f2 *>(&C.c[p][n][0]);
 }
@@ -60,15 +86,16 @@ __device__ __forceinline__ f2 lo2(const ChebF32 &C, int p, int n) {
 struct Setup32 {
     int64_t tau, ch;
     int32_t Ft[3];
-    float scale[32];
-    float nn[32];
+    float sch[32], scl[32];          // |tau||sigma| / (4 pi) as an FP32 pair
+    float nnh[32], nnl[32];          // n_tau . n_sigma as an FP32 pair
     int base[32];
     int valid[32];
-    float f0[32];
-    float D[32][3];
+    float f0h[32], f0l[32];  // frac(R0 / dt) as an FP32 pair
+    float Dh[32][3];         // unit vector (c_tau - c_sigma) / R0 as an FP32 pair
+    float Dl[32][3];
     float R0[32];
     float dqy[32][7][3];
-    float curl[32][9];
+    float cch[32][9], ccl[32][9];   // curl_a(tau) . curl_b(sigma) as FP32 pairs
 };
 
 // (psi, psi~) of the ten lag-class panels (C1: 3, C2: 4, C3: 3) at argument
@@ -78,7 +105,8 @@ struct Setup32 {
 // from n = NLOW-1 down to 0 from the kept T_n. Small terms therefore enter
 // before the large leading ones, and the rounding of the leading coefficients
 // does not become a fixed perturbation of psi, which the quadrature would not
-// average away and the cancellation in the odd prototype would amplify.
+// average away and the cancellation in the odd prototype would amplify. The
+// last three additions (n = 2, 1, 0) carry a Kahan compensation term.
 constexpr int NLOW = 8;
 __device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10]) {
     f2 T[NLOW];
@@ -112,7 +140,18 @@ __device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10
         for (int n = 0; n < NCHEB_LO; ++n) a = fma2(lo2(C, j, n), T[n], a);
         a = fma2(pk(1.f, 1.f), hi[j], a);
 #pragma unroll
-        for (int n = NLOW - 1; n >= 0; --n) a = fma2(coef2(C, j, n), T[n], a);
+        for (int n = NLOW - 1; n >= 3; --n) a = fma2(coef2(C, j, n), T[n], a);
+        // the three largest terms with Kahan compensation: their partial sums
+        // are of the size of psi, and their FP32 roundings would otherwise
+        // dominate the error of the panel value
+        f2 y = mul2(coef2(C, j, 2), T[2]);
+        f2 t = add2(a, y);
+        f2 nc = sub2(y, sub2(t, a));  // minus the rounding error of t
+        a = t;
+        y = fma2(coef2(C, j, 1), T[1], nc);
+        t = add2(a, y);
+        nc = sub2(y, sub2(t, a));
+        a = add2(t, add2(coef2(C, j, 0), nc));
         v[j] = a;
     }
 }
@@ -153,25 +192,51 @@ __device__ __forceinline__ void quad_packed(const FarArgs &A, const ChebF32 &C, 
 #pragma unroll
     for (int s = 0; s < NS; ++s) { a01[s] = 0ull; a2s[s] = 0ull; }
     const int valid = su.valid[lane];
-    const float f0 = su.f0[lane], R0 = su.R0[lane];
-    const float D0 = su.D[lane][0], D1 = su.D[lane][1], D2 = su.D[lane][2];
-    const float inv_dt = (float)A.lt.inv_dt;
+    const float f0h = su.f0h[lane], f0l = su.f0l[lane], R0 = su.R0[lane];
+    const float Dh0 = su.Dh[lane][0], Dh1 = su.Dh[lane][1], Dh2 = su.Dh[lane][2];
+    const float Dl0 = su.Dl[lane][0], Dl1 = su.Dl[lane][1], Dl2 = su.Dl[lane][2];
+    const float ih = (float)A.lt.inv_dt, il = (float)(A.lt.inv_dt - (double)ih);
 #pragma unroll 1
     for (int y = 0; y < 7; ++y) {
+        // r - R0 = u + e_perp^2 / ((R0 + u) + r) with u = D^.e, e the offset
+        // difference and e_perp^2 = e.e - u^2; the FP32 rounding of the
+        // small correction term is harmless, and u carries the low part of
+        // the unit vector D^
         const float e0 = dx0 - su.dqy[lane][y][0];
         const float e1 = dx1 - su.dqy[lane][y][1];
         const float e2 = dx2 - su.dqy[lane][y][2];
-        const float sv = 2.f * (D0 * e0 + D1 * e1 + D2 * e2) + (e0 * e0 + e1 * e1 + e2 * e2);
-        const float dr = sv * __frcp_rn(R0 + sqrtf(fmaxf(R0 * R0 + sv, 0.f)));
-        const float ir = __frcp_rn(R0 + dr);
-        const float q = f0 + dr * inv_dt;
-        const float cf = floorf(q);
+        const float u = fmaf(Dh2, e2, fmaf(Dh1, e1, Dh0 * e0));
+        const float ul = fmaf(Dl2, e2, fmaf(Dl1, e1, Dl0 * e0));
+        const float ee = fmaf(e2, e2, fmaf(e1, e1, e0 * e0));
+        const float ep = fmaf(-u, u, ee);
+        const float tt = R0 + u;
+        const float rr = sqrtf(fmaxf(fmaf(tt, tt, ep), 0.f));
+        const float corr = ep * __frcp_rn(tt + rr);
+        const float ir = __frcp_rn(tt + corr);
+        // q = f0 + (u + corr + ul) / dt as an FP32 pair (two-sums and exact
+        // product error); floor of the high part, fraction plus low part
+        const float du = u + corr;
+        const float b1 = du - u;
+        const float de = (u - (du - b1)) + (corr - b1);
+        const float wh = du * ih;
+        const float wl = fmaf(du, ih, -wh);
+        const float sh = f0h + wh;
+        const float b2 = sh - f0h;
+        const float se = (f0h - (sh - b2)) + (wh - b2);
+        const float low = (se + (wl + fmaf(de + ul, ih, du * il))) + f0l;
+        const float cf = floorf(sh);
         int cell = (int)cf;
-        const float u = q - cf;
-        const float x = u + u - 1.f;
-        const float wr = valid ? A.rw32[y] * ir : 0.f;
-        const f2 F01 = pk(wr * A.rl32[3 * y], wr * A.rl32[3 * y + 1]);
-        const f2 F2W = pk(wr * A.rl32[3 * y + 2], wr);
+        const float uq = (sh - cf) + low;
+        const float x = uq + uq - 1.f;
+        // weights w_y lambda_b(y) and w_y carried as FP32 pairs, so that
+        // their rounding is not a fixed bias shared by all element pairs
+        const float irv = valid ? ir : 0.f;
+        const float F0 = fmaf(irv, A.gwl[3 * y], irv * A.gwh[3 * y]);
+        const float F1 = fmaf(irv, A.gwl[3 * y + 1], irv * A.gwh[3 * y + 1]);
+        const float F2 = fmaf(irv, A.gwl[3 * y + 2], irv * A.gwh[3 * y + 2]);
+        const float wr = fmaf(irv, A.wwl[y], irv * A.wwh[y]);
+        const f2 F01 = pk(F0, F1);
+        const f2 F2W = pk(F2, wr);
         if (cell < -OFF || cell > OFF) {
             if (valid) A.status[0] = ST_OFF_RANGE;
             cell = 0;
@@ -203,7 +268,9 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
     const int64_t sg = ch * 32 + lane;
     const int32_t Ft0 = g.F[3 * tau], Ft1 = g.F[3 * tau + 1], Ft2 = g.F[3 * tau + 2];
     int valid = 0, base = 0;
-    float f0 = 0.f, R0 = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f, scale = 0.f, nn = 0.f;
+    float f0h = 0.f, f0l = 0.f, R0 = 1.f;
+    float Dh[3] = {0.f, 0.f, 0.f}, Dl[3] = {0.f, 0.f, 0.f};
+    double scale = 0.0, nn = 0.0, cc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (sg < E) {
         const int32_t *B = g.F + 3 * sg;
         int shared = 0;
@@ -216,20 +283,39 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
         const double q0 = r0 * A.lt.inv_dt;
         const double fb = floor(q0);
         base = (int)fb;
-        f0 = (float)(q0 - fb);
-        R0 = (float)r0; D0 = (float)d0; D1 = (float)d1; D2 = (float)d2;
-        const float *gt = g.geo32 + 16 * tau, *gs = g.geo32 + 16 * sg;
-        scale = gt[3] * gs[3] * 0.07957747f;  // 1/(4 pi)
+        const double f0 = q0 - fb;
+        f0h = (float)f0;
+        f0l = (float)(f0 - (double)f0h);
+        R0 = (float)r0;
+        const double ir0 = 1.0 / r0;
+        const double dd[3] = {d0 * ir0, d1 * ir0, d2 * ir0};
+        for (int k = 0; k < 3; ++k) {
+            Dh[k] = (float)dd[k];
+            Dl[k] = (float)(dd[k] - (double)Dh[k]);
+        }
+        // geometric factors of the element pair in FP64, kept as FP32 pairs:
+        // the n.n and curl.curl parts of a block cancel to a small fraction
+        // of either, so their FP32 rounding would be amplified
+        const double *gt = g.geo64 + 16 * tau, *gs = g.geo64 + 16 * sg;
+        scale = gt[3] * gs[3] * 0.079577471545947668;  // 1/(4 pi)
         nn = gt[0] * gs[0] + gt[1] * gs[1] + gt[2] * gs[2];
-        for (int k = 0; k < 9; ++k) su.curl[lane][k] = gs[4 + k];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                cc[3 * a + b] = gt[4 + 3 * a] * gs[4 + 3 * b] + gt[5 + 3 * a] * gs[5 + 3 * b] + gt[6 + 3 * a] * gs[6 + 3 * b];
         for (int k = 0; k < 21; ++k) su.dqy[lane][k / 3][k % 3] = g.dq32[sg * 21 + k];
     } else {
-        for (int k = 0; k < 9; ++k) su.curl[lane][k] = 0.f;
         for (int k = 0; k < 21; ++k) su.dqy[lane][k / 3][k % 3] = 0.f;
     }
-    su.valid[lane] = valid; su.base[lane] = base; su.f0[lane] = f0; su.R0[lane] = R0;
-    su.D[lane][0] = D0; su.D[lane][1] = D1; su.D[lane][2] = D2;
-    su.scale[lane] = scale; su.nn[lane] = nn;
+    su.sch[lane] = (float)scale;
+    su.scl[lane] = (float)(scale - (double)su.sch[lane]);
+    su.nnh[lane] = (float)nn;
+    su.nnl[lane] = (float)(nn - (double)su.nnh[lane]);
+    for (int k = 0; k < 9; ++k) {
+        su.cch[lane][k] = (float)cc[k];
+        su.ccl[lane][k] = (float)(cc[k] - (double)su.cch[lane][k]);
+    }
+    su.valid[lane] = valid; su.base[lane] = base; su.f0h[lane] = f0h; su.f0l[lane] = f0l; su.R0[lane] = R0;
+    for (int k = 0; k < 3; ++k) { su.Dh[lane][k] = Dh[k]; su.Dl[lane][k] = Dl[k]; }
     if (lane == 0) { su.tau = tau; su.ch = ch; su.Ft[0] = Ft0; su.Ft[1] = Ft1; su.Ft[2] = Ft2; }
 }
 
@@ -242,7 +328,7 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Setup32 *sub = reinterpret_cast<Setup32 *>(smem_raw);                                       // [2]
     float *red = reinterpret_cast<float *>(smem_raw + ((2 * sizeof(Setup32) + 15) / 16) * 16);  // [7][32][NS][4]
-    float *Lb = red + (size_t)F32_XW * 32 * NS * 4;                                             // [32][NS][9]
+    FF *Lb = reinterpret_cast<FF *>(red + (size_t)F32_XW * 32 * NS * 4);                        // [32][NS][9]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = w == F32_XW;
     const int xw = w;
@@ -274,32 +360,62 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
         __syncthreads();
         for (int k = threadIdx.x; k < 32 * NS; k += F32_THREADS_ALL) {
             const int sl = k / NS, s = k % NS;
-            float Sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, St = 0.f;
+            FF *lp = Lb + ((size_t)sl * NS + s) * 9;
+            f2 q01[7], q2s[7];
+            unsigned long long any = 0ull;
 #pragma unroll
             for (int x = 0; x < 7; ++x) {
-                const float *q = red + ((size_t)(x * 32 + sl) * NS + s) * 4;
-                const float wx = A.rw32[x];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float ga = wx * A.rl32[3 * x + a];
-#pragma unroll
-                    for (int b = 0; b < 3; ++b) Sab[a][b] += ga * q[b];
-                }
-                St += wx * q[3];
+                const f2 *q = reinterpret_cast<const f2 *>(red + ((size_t)(x * 32 + sl) * NS + s) * 4);
+                q01[x] = q[0];
+                q2s[x] = q[1];
+                any |= q01[x] | q2s[x];
             }
-            const float *gt = g.geo32 + 16 * su.tau + 4, *gs = su.curl[sl];
-            const float sc = su.scale[sl], nn = su.nn[sl];
-            float *lp = Lb + ((size_t)sl * NS + s) * 9;
+            if (any == 0ull) {  // slot not reached by this element pair
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+                for (int i = 0; i < 9; ++i) lp[i] = FF{0.f, 0.f};
+                continue;
+            }
+            // S_ab = sum_x w_x lambda_a(x) t_b(x) and S~ = sum_x w_x s~(x)
+            // as FP32 pairs: packed (S_a0, S_a1) for a = 0..2, (S_02, S_12)
+            // and (S_22, S~)
+            f2 h[5] = {0ull, 0ull, 0ull, 0ull, 0ull}, l[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-                for (int b = 0; b < 3; ++b) {
-                    const float cc = gt[3 * a] * gs[3 * b] + gt[3 * a + 1] * gs[3 * b + 1] + gt[3 * a + 2] * gs[3 * b + 2];
-                    lp[3 * a + b] = sc * (nn * Sab[a][b] + cc * St);
-                }
+            for (int x = 0; x < 7; ++x) {
+                const float g0h = A.gwh[3 * x], g1h = A.gwh[3 * x + 1], g2h = A.gwh[3 * x + 2];
+                const float g0l = A.gwl[3 * x], g1l = A.gwl[3 * x + 1], g2l = A.gwl[3 * x + 2];
+                float t2, st;
+                upk(q2s[x], t2, st);
+                ff_acc(h[0], l[0], pk(g0h, g0h), pk(g0l, g0l), q01[x]);
+                ff_acc(h[1], l[1], pk(g1h, g1h), pk(g1l, g1l), q01[x]);
+                ff_acc(h[2], l[2], pk(g2h, g2h), pk(g2l, g2l), q01[x]);
+                ff_acc(h[3], l[3], pk(g0h, g1h), pk(g0l, g1l), pk(t2, t2));
+                ff_acc(h[4], l[4], pk(g2h, A.wwh[x]), pk(g2l, A.wwl[x]), q2s[x]);
+            }
+            float Sh[9], Sl[9], Th, Tl;
+            upk(h[0], Sh[0], Sh[1]); upk(l[0], Sl[0], Sl[1]);
+            upk(h[1], Sh[3], Sh[4]); upk(l[1], Sl[3], Sl[4]);
+            upk(h[2], Sh[6], Sh[7]); upk(l[2], Sl[6], Sl[7]);
+            upk(h[3], Sh[2], Sh[5]); upk(l[3], Sl[2], Sl[5]);
+            upk(h[4], Sh[8], Th); upk(l[4], Sl[8], Tl);
+            // L_ab = scale (n.n S_ab + curl_a.curl_b S~) in FP32-pair arithmetic
+            const float sch = su.sch[sl], scl = su.scl[sl], nh = su.nnh[sl], nl = su.nnl[sl];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float ch = su.cch[sl][i], cl = su.ccl[sl][i];
+                const float ph = nh * Sh[i];
+                const float pl = fmaf(nh, Sh[i], -ph) + fmaf(nh, Sl[i], nl * Sh[i]);
+                const float qh = ch * Th;
+                const float ql = fmaf(ch, Th, -qh) + fmaf(ch, Tl, cl * Th);
+                const float th = ph + qh;
+                const float bb = th - ph;
+                const float tl = ((ph - (th - bb)) + (qh - bb)) + (pl + ql);
+                const float lh = sch * th;
+                const float ll = fmaf(sch, th, -lh) + fmaf(sch, tl, scl * th);
+                lp[i] = FF{lh, ll};
+            }
         }
         __syncthreads();
-        scatter_chunk<float, OFF, F32_THREADS_ALL, Setup32, false>(A, su.ch, su.Ft[0], su.Ft[1], su.Ft[2], su, Lb);
+        scatter_chunk<FF, OFF, F32_THREADS_ALL, Setup32, false>(A, su.ch, su.Ft[0], su.Ft[1], su.Ft[2], su, Lb);
         __syncthreads();
     }
 }
@@ -307,7 +423,8 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
 template <int OFF>
 static void launch32(const FarArgs &a, const ChebF32 &c32, int grid, cudaStream_t st) {
     constexpr int NS = slot0<OFF>(NLAG);
-    const size_t smem = ((2 * sizeof(Setup32) + 15) / 16) * 16 + sizeof(float) * ((size_t)F32_XW * 32 * NS * 4 + 32 * NS * 9);
+    const size_t smem = ((2 * sizeof(Setup32) + 15) / 16) * 16 + sizeof(float) * (size_t)F32_XW * 32 * NS * 4 +
+                        sizeof(FF) * 32 * NS * 9;
     cudaFuncSetAttribute(far32_kernel<OFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     far32_kernel<OFF><<<grid, F32_THREADS_ALL, smem, st>>>(a, c32);
 }

@@ -58,6 +58,24 @@ __device__ __forceinline__ R rule_l(const FarArgs &A, int k) {
 // trial vertex (host-built per-chunk plan) and add them, read-modify-write
 // without atomics, into the FP64 lag windows of rows F[tau][a]. Lb holds
 // [32 sigma][NS slots][9] values; su the element-pair setup of the chunk.
+// Lb element types: float or double values, or FP32 pairs (hi, lo) summed
+// with an error-free two-sum
+struct FF {
+    float h, l;
+};
+__device__ __forceinline__ void lb_add(float &s, float v) { s += v; }
+__device__ __forceinline__ void lb_add(double &s, double v) { s += v; }
+__device__ __forceinline__ void lb_add(FF &s, FF v) {
+    const float t = s.h + v.h;
+    const float bb = t - s.h;
+    const float e = (s.h - (t - bb)) + (v.h - bb);
+    s.l = (s.l + v.l) + e;
+    s.h = t;
+}
+__device__ __forceinline__ double lb_value(float s) { return (double)s; }
+__device__ __forceinline__ double lb_value(double s) { return s; }
+__device__ __forceinline__ double lb_value(FF s) { return (double)s.h + (double)s.l; }
+
 template <typename R, int OFF, int NTHREADS, typename Setup, bool WITH_SPEC = true>
 __device__ __forceinline__ void scatter_chunk(const FarArgs &A, int64_t ch, int32_t Ft0, int32_t Ft1, int32_t Ft2,
                                               const Setup &su, const R *Lb) {
@@ -102,28 +120,28 @@ __device__ __forceinline__ void scatter_chunk(const FarArgs &A, int64_t ch, int3
             for (int k = 0; k < KW_MAX; ++k) {
                 const int d = wlo + k;
                 if (d < dmn || d > dmx) continue;
-                R sum = R(0);
+                R sum{};
                 for (int x = s0; x < s1; ++x) {
                     const int src = A.chunk_src[x], sl = src / 3, b = src % 3;
                     if (!su.valid[sl]) continue;
                     const int slot = d - (su.base[sl] - rho - (P - 1) - OFF);
                     if (slot < 0 || slot >= K) continue;
-                    sum += Lb[((size_t)sl * NS + so + slot) * 9 + 3 * a + b];
+                    lb_add(sum, Lb[((size_t)sl * NS + so + slot) * 9 + 3 * a + b]);
                 }
-                dst[k] = cur[k] + (double)sum;
+                dst[k] = cur[k] + lb_value(sum);
             }
         } else {
             const int sbit = c - NLAG;
             if (!((A.smask[l * M + j] >> sbit) & 1u)) continue;
             const int so = slot0<OFF>(C3) + cls_K<OFF>(C3) + sbit;
-            R sum = R(0);
+            R sum{};
             for (int x = s0; x < s1; ++x) {
                 const int src = A.chunk_src[x], sl = src / 3, b = src % 3;
                 if (!su.valid[sl]) continue;
-                sum += Lb[((size_t)sl * NS + so) * 9 + 3 * a + b];
+                lb_add(sum, Lb[((size_t)sl * NS + so) * 9 + 3 * a + b]);
             }
             double *dst = A.dense_spec + (sbit * MM + l * M + j);
-            *dst += (double)sum;
+            *dst += lb_value(sum);
         }
     }
 }

@@ -4,9 +4,7 @@ against the oracle's matvec over its own FP64 blocks.
 
 Error per block row k: ||y_k - y_k^oracle|| / ||y_k^oracle|| over the rows
 whose norm is at least 1e-3 of the largest; every row against the largest.
-Tolerances follow the block parity: FP64 path 1e-10, mixed path 1e-6 on the
-small meshes and 2e-6 at 20480 triangles (the mixed block error there reaches
-1.4e-6, an open item).
+Tolerances follow the block parity: FP64 path 1e-10, mixed path 1e-6.
 """
 import numpy as np
 import pytest
@@ -77,7 +75,7 @@ def test_matvec_sphere20480_sampled(td):
     rows = np.sort(np.random.default_rng(1).choice(w.M, size=3, replace=False))
     rel, ab = _run(td, w.verts, w.tris, w.t, 1, rows=rows)
     print("sphere20480 prec 1 rows %s: max rel %.3e, abs %.3e" % (rows, rel, ab))
-    assert rel < 2e-6 and ab < 2e-6
+    assert rel < 1e-6 and ab < 1e-6
 
 
 def test_matvec_errors(td):
