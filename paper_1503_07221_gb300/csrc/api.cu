@@ -177,6 +177,7 @@ struct tdbem_mesh {
     int NB = 0;
     std::vector<std::vector<int32_t>> colors;
     std::vector<int32_t> chunk_vptr, chunk_vert, chunk_sptr, chunk_src;
+    int max_nv = 0;
     int64_t nchunks = 0;
     double diam = 0.0, max_dq = 0.0, max_star = 0.0, coord_scale = 0.0;
     double rule_L[7][3], rule_W[7];
@@ -326,6 +327,7 @@ static tdbem_status build_mesh(tdbem_mesh &m) {
             m.chunk_src.insert(m.chunk_src.end(), kv.second.begin(), kv.second.end());
         }
         m.chunk_vptr[ch + 1] = (int32_t)m.chunk_vert.size();
+        m.max_nv = std::max(m.max_nv, m.chunk_vptr[ch + 1] - m.chunk_vptr[ch]);
     }
     m.chunk_sptr.push_back((int32_t)m.chunk_src.size());
     // diameter (largest vertex distance) and largest star diameter
@@ -815,6 +817,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         fa.chunk_vptr = (const int32_t *)A->chunk_vptr.p; fa.chunk_vert = (const int32_t *)A->chunk_vert.p;
         fa.chunk_sptr = (const int32_t *)A->chunk_sptr.p; fa.chunk_src = (const int32_t *)A->chunk_src.p;
         fa.nchunks = m.nchunks;
+        fa.max_nv = m.max_nv;
         fa.rule_w = (const float *)A->rule_w.p; fa.rule_l = (const float *)A->rule_l.p;
         fa.rule_w64 = (const double *)A->rule_w64.p; fa.rule_l64 = (const double *)A->rule_l64.p;
         fa.dense = (double *)A->dense.p; fa.dense_spec = (double *)A->dense_spec.p; fa.KW = A->KW;

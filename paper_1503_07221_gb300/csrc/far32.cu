@@ -319,6 +319,117 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
     if (lane == 0) { su.tau = tau; su.ch = ch; su.Ft[0] = Ft0; su.Ft[1] = Ft1; su.Ft[2] = Ft2; }
 }
 
+// Staging of the current chunk's scatter inputs, issued by the producer warp
+// while the compute warps run the quadrature: the lag-window bounds of every
+// (trial vertex, test corner, class) item and the window values themselves
+// (asynchronous 8-byte copies into shared memory), so that the scatter phase
+// reads only shared memory and writes global memory.
+__device__ __forceinline__ void stage_scatter(const FarArgs &A, const Setup32 &su, int lane, double *stg,
+                                              int16_t *swlo, int16_t *swhi) {
+    const Geo &g = A.g;
+    const int64_t M = g.M, MM = M * M;
+    const int KW = A.KW;
+    const int v0 = A.chunk_vptr[su.ch], nitems = (A.chunk_vptr[su.ch + 1] - v0) * 3 * NLAG;
+    constexpr int SPL = 8;  // items per lane per batch: independent loads in flight
+    for (int b0 = 0; b0 < nitems; b0 += 32 * SPL) {
+        int64_t o[SPL];
+#pragma unroll
+        for (int q = 0; q < SPL; ++q) {
+            const int it = b0 + q * 32 + lane;
+            o[q] = -1;
+            if (it < nitems) {
+                const int v = it / (3 * NLAG), rem = it % (3 * NLAG);
+                const int a = rem / NLAG, c = rem % NLAG;
+                o[q] = c * MM + (int64_t)su.Ft[a] * M + A.chunk_vert[v0 + v];
+            }
+        }
+        int16_t wl[SPL], wh[SPL];
+#pragma unroll
+        for (int q = 0; q < SPL; ++q) {
+            wl[q] = o[q] >= 0 ? A.dlo[o[q]] : (int16_t)0;
+            wh[q] = o[q] >= 0 ? A.dhi[o[q]] : (int16_t)0;
+        }
+#pragma unroll
+        for (int q = 0; q < SPL; ++q) {
+            if (o[q] < 0) continue;
+            const int it = b0 + q * 32 + lane;
+            const double *src = A.dense + o[q] * KW;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(stg + (size_t)it * KW);
+            for (int k = 0; k < KW; ++k)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst + 8 * k), "l"(src + k));
+        }
+#pragma unroll
+        for (int q = 0; q < SPL; ++q) {
+            if (o[q] < 0) continue;
+            const int it = b0 + q * 32 + lane;
+            swlo[it] = wl[q];
+            swhi[it] = wh[q];
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Scatter of one chunk's lag-class values into the FP64 lag windows of the
+// CTA's test rows from the staged windows: thread per (trial vertex, test
+// corner, class), sums over the chunk's triangles at that vertex.
+template <int OFF>
+__device__ __forceinline__ void scatter_staged(const FarArgs &A, const Setup32 &su, const FF *Lb,
+                                               const double *stg, const int16_t *swlo, const int16_t *swhi) {
+    constexpr int NS = slot0<OFF>(NLAG);
+    const Geo &g = A.g;
+    const int64_t M = g.M, MM = M * M;
+    const int KW = A.KW;
+    const int v0 = A.chunk_vptr[su.ch], nitems = (A.chunk_vptr[su.ch + 1] - v0) * 3 * NLAG;
+    for (int it = threadIdx.x; it < nitems; it += F32_THREADS_ALL) {
+        const int v = it / (3 * NLAG), rem = it % (3 * NLAG);
+        const int a = rem / NLAG, c = rem % NLAG;
+        const int s0 = A.chunk_sptr[v0 + v], s1 = A.chunk_sptr[v0 + v + 1];
+        const int P = cls_P(c), K = 2 * OFF + P;
+        const int rho = A.lt.rho[c];
+        const int so = c == C1 ? slot0<OFF>(C1) : c == C2 ? slot0<OFF>(C2) : slot0<OFF>(C3);
+        const int wlo = swlo[it], whi = swhi[it];
+        double *dst = A.dense + (c * MM + (int64_t)su.Ft[a] * M + A.chunk_vert[v0 + v]) * KW;
+        const double *cur = stg + (size_t)it * KW;
+        // the vertex's triangles in this chunk, up to 8 per batch, in registers
+        constexpr int MAXS = 8;
+        for (int x0 = s0; x0 < s1; x0 += MAXS) {
+            int lbi[MAXS], off[MAXS];
+            bool has[MAXS];
+            int dmn = 1 << 30, dmx = -(1 << 30);
+#pragma unroll
+            for (int q = 0; q < MAXS; ++q) {
+                has[q] = false;
+                lbi[q] = 0;
+                off[q] = 0;
+                if (x0 + q < s1) {
+                    const int src = A.chunk_src[x0 + q], sl = src / 3, b = src % 3;
+                    if (su.valid[sl]) {
+                        has[q] = true;
+                        off[q] = su.base[sl] - rho - (P - 1) - OFF;
+                        lbi[q] = (sl * NS + so) * 9 + 3 * a + b;
+                        dmn = min(dmn, off[q]);
+                        dmx = max(dmx, off[q] + K - 1);
+                    }
+                }
+            }
+            dmn = max(dmn, wlo);
+            dmx = min(min(dmx, whi), wlo + KW - 1);
+            for (int d = dmn; d <= dmx; ++d) {
+                FF sum{};
+#pragma unroll
+                for (int q = 0; q < MAXS; ++q) {
+                    const int slot = d - off[q];
+                    if (has[q] && slot >= 0 && slot < K) lb_add(sum, Lb[lbi[q] + slot * 9]);
+                }
+                // first batch adds to the staged value, later ones to what the
+                // previous batch stored
+                const double base_v = x0 == s0 ? cur[d - wlo] : dst[d - wlo];
+                dst[d - wlo] = base_v + lb_value(sum);
+            }
+        }
+    }
+}
+
 // Special blocks (cell 0 and the first/last-row corner) are not evaluated
 // here: the few far pairs that reach them go through the FP64 pass in near.cu.
 template <int OFF>
@@ -329,6 +440,9 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
     Setup32 *sub = reinterpret_cast<Setup32 *>(smem_raw);                                       // [2]
     float *red = reinterpret_cast<float *>(smem_raw + ((2 * sizeof(Setup32) + 15) / 16) * 16);  // [7][32][NS][4]
     FF *Lb = reinterpret_cast<FF *>(red + (size_t)F32_XW * 32 * NS * 4);                        // [32][NS][9]
+    double *stg = reinterpret_cast<double *>(Lb + (size_t)32 * NS * 9);                        // [max_nv * 9][KW]
+    int16_t *swlo = reinterpret_cast<int16_t *>(stg + (size_t)A.max_nv * 3 * NLAG * A.KW);     // [max_nv * 9]
+    int16_t *swhi = swlo + A.max_nv * 3 * NLAG;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = w == F32_XW;
     const int xw = w;
@@ -344,10 +458,12 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
     for (int64_t it = 0; it < nit; ++it) {
         Setup32 &su = sub[it & 1];
         if (producer) {
+            stage_scatter(A, su, lane, stg, swlo, swhi);
             if (it + 1 < nit) {
                 const int64_t t2 = A.color_tris[blockIdx.x + ((it + 1) / nch) * gridDim.x];
                 chunk_setup(A, t2, (it + 1) % nch, lane, sub[(it + 1) & 1]);
             }
+            asm volatile("cp.async.wait_all;" ::: "memory");
         } else {
             if (su.tau != cur_tau) {
                 cur_tau = su.tau;
@@ -415,7 +531,7 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebF32 C) {
             }
         }
         __syncthreads();
-        scatter_chunk<FF, OFF, F32_THREADS_ALL, Setup32, false>(A, su.ch, su.Ft[0], su.Ft[1], su.Ft[2], su, Lb);
+        scatter_staged<OFF>(A, su, Lb, stg, swlo, swhi);
         __syncthreads();
     }
 }
@@ -424,7 +540,7 @@ template <int OFF>
 static void launch32(const FarArgs &a, const ChebF32 &c32, int grid, cudaStream_t st) {
     constexpr int NS = slot0<OFF>(NLAG);
     const size_t smem = ((2 * sizeof(Setup32) + 15) / 16) * 16 + sizeof(float) * (size_t)F32_XW * 32 * NS * 4 +
-                        sizeof(FF) * 32 * NS * 9;
+                        sizeof(FF) * 32 * NS * 9 + (sizeof(double) * a.KW + 2 * sizeof(int16_t)) * (size_t)a.max_nv * 3 * NLAG;
     cudaFuncSetAttribute(far32_kernel<OFF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     far32_kernel<OFF><<<grid, F32_THREADS_ALL, smem, st>>>(a, c32);
 }

@@ -146,6 +146,7 @@ struct FarArgs {
     const double *rule_l64;
     float rw32[7];             // 7-point rule weights and barycentrics by value
     float rl32[21];            // (constant bank in the FP32 kernel)
+    int max_nv;                // most trial vertices in one chunk
     float gwh[21], gwl[21];    // w_k lambda_a(p_k) as FP32 pairs (hi, lo), index 3k + a
     float wwh[7], wwl[7];      // w_k as FP32 pairs
     double *dense;             // 3 x M x M x KW lag windows, FP64 accumulation
