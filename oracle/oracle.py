@@ -91,6 +91,45 @@ def num_threads():
     return lib().or_num_threads()
 
 
+# ---------------------------------------------------------------- data g --
+# Neumann data g(x, t) of the boundary integral equation W phi = g (Eq. BIE),
+# by kind:
+#   0  plane wave u_inc = exp(-(t - x.d - c)^2 / (2 w^2)), params (dx, dy, dz,
+#      c, w): g = -d/dn u_inc = (d.n) f'(t - x.d), the sound-hard condition
+#   1  g(t) Y_0^0 with g(t) = sin(3t) t^2 exp(-t) (Sec. 6.1, first test)
+#   2  g(t) Y_1^0(x) with g(t) = sin(2 pi t) t^3 exp(-2t) (Sec. 6.1, second)
+Y00 = 1.0 / np.sqrt(4.0 * np.pi)
+Y10 = np.sqrt(3.0 / (4.0 * np.pi))
+
+
+def g_time(kind, t):
+    t = np.asarray(t, dtype=np.float64)
+    if kind == 1:
+        return np.where(t > 0, np.sin(3 * t) * t * t * np.exp(-t), 0.0)
+    if kind == 2:
+        return np.where(t > 0, np.sin(2 * np.pi * t) * t ** 3 * np.exp(-2 * t), 0.0)
+    raise ValueError(kind)
+
+
+def g_data(kind, params, x, n, t):
+    """g at points x (..., 3) with unit normals n (..., 3) and times t (T,):
+    array (..., T)."""
+    x = np.asarray(x, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    if kind == 0:
+        d = np.asarray(params[:3], dtype=np.float64)
+        c, w = float(params[3]), float(params[4])
+        s = t[None, :] - (x.reshape(-1, 3) @ d)[:, None] - c
+        fp = -s / (w * w) * np.exp(-0.5 * (s / w) ** 2)
+        dn = n.reshape(-1, 3) @ d
+        return (dn[:, None] * fp).reshape(x.shape[:-1] + (t.size,))
+    if kind == 1:
+        return np.broadcast_to(Y00 * g_time(1, t), x.shape[:-1] + (t.size,)).copy()
+    if kind == 2:
+        return (Y10 * x[..., 2])[..., None] * g_time(2, t)
+    raise ValueError(kind)
+
+
 class Oracle:
     """FP64 CPU oracle bound to one mesh and time grid.
 
@@ -257,6 +296,66 @@ class Oracle:
                 for r, (c, f, n) in enumerate(R[b]):
                     y[kb, rows[r]] += np.dot(f + n, x[ib, c])
         return y
+
+    def rhs(self, kind, params=(), nt=16, sub=4):
+        """Right-hand side g_k(l) = int_0^T int_Gamma g(x,t) phi_l(x)
+        bdot_k(t) dGamma dt of the linear system (Sec. 3, Eq. of the
+        partitioned system), as an (N, M) array: the 7-point rule on every
+        triangle in space, composite Gauss-Legendre in time on every
+        [t_j, t_{j+1}] (the breakpoints of every bdot_k), `sub` panels of
+        `nt` points each."""
+        bary, w7 = rule7()
+        P = self.V[self.F]                                     # (E, 3, 3)
+        X = np.einsum("pa,eaj->epj", bary, P)                  # (E, 7, 3)
+        cr = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+        area = 0.5 * np.linalg.norm(cr, axis=1)
+        nrm = cr / (2.0 * area[:, None])
+        xg, wg = gauss_legendre(nt)
+        t = self.t
+        s_list, w_list = [], []
+        for j in range(t.size - 1):
+            h = (t[j + 1] - t[j]) / sub
+            for q in range(sub):
+                a0 = t[j] + q * h
+                s_list.append(a0 + h * xg)
+                w_list.append(h * wg)
+        s_n = np.concatenate(s_list)
+        w_n = np.concatenate(w_list)
+        G = g_data(kind, params, X, np.repeat(nrm[:, None, :], 7, axis=1), s_n)  # (E, 7, Ns)
+        out = np.zeros((self.N, self.M))
+        coef = area[:, None, None] * w7[None, :, None] * bary[None, :, :]     # (E, 7, 3)
+        for k in range(self.N):
+            bd = self.basis(k, 0, s_n)[:, 1]
+            H = G @ (w_n * bd)                                  # (E, 7)
+            contrib = np.einsum("ep,epa->ea", H, coef)          # (E, 3)
+            np.add.at(out[k], self.F.ravel(), contrib.ravel())
+        return out
+
+    def full_matrix(self):
+        """The whole space-time matrix (N M x N M) of Eq. Apartitioned, block
+        (k, i) at rows k M.., columns i M.., from the listed blocks through
+        block_source (small cases only)."""
+        N, M = self.N, self.M
+        nb = self.num_blocks()
+        R = self.assemble_rows(np.arange(M), np.arange(nb))
+        D = []
+        for b in range(nb):
+            B = np.zeros((M, M))
+            for l, (c, f, n) in enumerate(R[b]):
+                B[l, c] = f + n
+            D.append(B)
+        A = np.zeros((N * M, N * M))
+        for kb in range(N):
+            for ib in range(N):
+                b = self.block_source(kb, ib)
+                if b is not None:
+                    A[kb * M:(kb + 1) * M, ib * M:(ib + 1) * M] = D[b]
+        return A
+
+    def solve_dense(self, g):
+        """alpha with A alpha = g by dense LU (numpy), shapes (N, M)."""
+        A = self.full_matrix()
+        return np.linalg.solve(A, np.asarray(g, dtype=np.float64).ravel()).reshape(self.N, self.M)
 
     def dense_block(self, blk):
         """The whole block as a dense M x M array (far + near), row = test vertex."""
