@@ -210,6 +210,39 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply(const tdbem_asm *a, const double *
 TDBEM_API tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *a, const double *x_dev, double *y_dev,
                                                       void *stream);
 
+/* Right-hand side of the linear system (Sec. 3): g_k(l) = int_0^T int_Gamma
+ * g(x,t) phi_l(x) bdot_k(t) dGamma dt for every time basis function k and
+ * vertex l, written to the caller-owned device array g_dev of N*M doubles
+ * (row k at [k*M, k*M + M)). FP64; 7-point rule on every triangle, composite
+ * Gauss-Legendre in time split at every grid point. Neumann data g by kind:
+ *   TDBEM_RHS_PLANE_WAVE: sound-hard scattering of u_inc = exp(-(t - x.d -
+ *     c0)^2 / (2 w^2)); params = {dx, dy, dz, c0, w} (nparams 5, d is
+ *     normalised), g = -du_inc/dn;
+ *   TDBEM_RHS_SPHERE_N0: g = Y_0^0 sin(3t) t^2 e^{-t} (Sec. 6.1), nparams 0;
+ *   TDBEM_RHS_SPHERE_N1: g = Y_1^0(x) sin(2 pi t) t^3 e^{-2t} (Sec. 6.1).
+ * Needs no assembly. Asynchronous on `stream`. TDBEM_E_INVALID_ARG for a NULL
+ * pointer, an unknown kind or bad parameters. */
+#define TDBEM_RHS_PLANE_WAVE 0
+#define TDBEM_RHS_SPHERE_N0 1
+#define TDBEM_RHS_SPHERE_N1 2
+TDBEM_API tdbem_status tdbem_rhs_assemble(const tdbem_asm *a, int32_t kind, const double *params,
+                                          int32_t nparams, double *g_dev, void *stream);
+
+/* Solve A alpha = g (the block-Hessenberg system of Eq. Apartitioned) by
+ * restarted GMRES(restart) (Sec. 4) with tdbem_hessenberg_apply as the
+ * product: zero initial guess, stop when ||g - A alpha|| <= tol ||g|| or after
+ * max_iter iterations. g and alpha are caller-owned device arrays of N*M
+ * doubles that must not overlap; the Krylov basis ((restart+1) N M doubles)
+ * is allocated through the registered allocator for the call and freed
+ * before it returns. On return *iters holds the iterations done and *rel_res
+ * the relative residual of alpha (either may be NULL). Synchronises the
+ * stream. TDBEM_E_NOT_ASSEMBLED before an assembly; TDBEM_E_INVALID_ARG for
+ * restart outside 1..62, tol <= 0, max_iter < 1, NULL or overlapping
+ * arrays; TDBEM_E_OOM if the basis cannot be allocated. */
+TDBEM_API tdbem_status tdbem_solve_gmres(const tdbem_asm *a, const double *g_dev, double *alpha_dev,
+                                         int32_t restart, double tol, int32_t max_iter, int32_t *iters,
+                                         double *rel_res, void *stream);
+
 /* Assembly counters and the per-phase device times of the last assembly. */
 TDBEM_API tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
 

@@ -1025,6 +1025,160 @@ tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x,
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_rhs_assemble(const tdbem_asm *A, int32_t kind, const double *params, int32_t nparams,
+                                double *g_dev, void *stream) {
+    if (!A || !g_dev) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    RhsParams prm{};
+    if (kind == TDBEM_RHS_PLANE_WAVE) {
+        if (!params || nparams != 5) return fail(TDBEM_E_INVALID_ARG, "plane wave takes 5 parameters (dx, dy, dz, c0, w)");
+        const double dn = sqrt(params[0] * params[0] + params[1] * params[1] + params[2] * params[2]);
+        if (!(dn > 0.0) || !(params[4] > 0.0) || !std::isfinite(params[3]))
+            return fail(TDBEM_E_INVALID_ARG, "plane wave needs a nonzero direction and a positive width");
+        for (int k = 0; k < 3; ++k) prm.p[k] = params[k] / dn;
+        prm.p[3] = params[3];
+        prm.p[4] = params[4];
+    } else if (kind == TDBEM_RHS_SPHERE_N0 || kind == TDBEM_RHS_SPHERE_N1) {
+        if (nparams != 0) return fail(TDBEM_E_INVALID_ARG, "this kind takes no parameters");
+    } else {
+        return fail(TDBEM_E_INVALID_ARG, "unknown right-hand side kind");
+    }
+    const tdbem_asm *Ac = A;
+    Geo g = make_geo(const_cast<tdbem_asm *>(Ac));
+    launch_rhs(g, (const double *)A->tgrid.p, (int)A->tg->N, A->tg->c, (const double *)A->rule_w64.p,
+               (const double *)A->rule_l64.p, (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 4, kind, prm,
+               g_dev, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return TDBEM_OK;
+}
+
+// Restarted GMRES(m) with classical Gram-Schmidt and one reorthogonalisation;
+// the Hessenberg least-squares problem is updated with Givens rotations on the
+// host. Zero initial guess.
+tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, int32_t restart, double tol,
+                               int32_t max_iter, int32_t *iters, double *rel_res, void *stream) {
+    if (!A || !g || !x) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    if (restart < 1 || restart > GM_MAXV - 2) return fail(TDBEM_E_INVALID_ARG, "restart must be in 1..62");
+    if (!(tol > 0.0) || max_iter < 1) return fail(TDBEM_E_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+    const int64_t n = A->tg->N * A->mesh->M;
+    const char *gb = (const char *)g, *xb = (const char *)x;
+    if (gb < xb + n * 8 && xb < gb + n * 8) return fail(TDBEM_E_INVALID_ARG, "g and x overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = restart;
+    DevBuf Vb, wb, pb, hb, sb;
+    tdbem_status s;
+    if ((s = dev_alloc(Vb, (size_t)(m + 1) * n * sizeof(double), st))) return s;
+    if ((s = dev_alloc(wb, (size_t)n * sizeof(double), st))) return s;
+    if ((s = dev_alloc(pb, (size_t)GM_BLOCKS * GM_MAXV * sizeof(double), st))) return s;
+    if ((s = dev_alloc(hb, (size_t)2 * GM_MAXV * sizeof(double), st))) return s;
+    if ((s = dev_alloc(sb, (size_t)GM_MAXV * sizeof(double), st))) return s;
+    double *V = (double *)Vb.p, *w = (double *)wb.p, *part = (double *)pb.p, *hd = (double *)hb.p, *sd = (double *)sb.p;
+    auto dot = [&](const double *Vv, int nv, const double *ww, double *hout) -> tdbem_status {
+        launch_multi_dot(Vv, n, nv, ww, n, part, hd, st);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(hout, hd, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return TDBEM_OK;
+    };
+    auto upload = [&](const double *hv, int nv) -> tdbem_status {
+        CUDA_TRY(cudaMemcpyAsync(sd, hv, nv * sizeof(double), cudaMemcpyHostToDevice, st));
+        return TDBEM_OK;
+    };
+    CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    double gn2 = 0.0;
+    if ((s = dot(g, 1, g, &gn2))) return s;
+    const double gnorm = sqrt(gn2);
+    int total = 0;
+    double rr = 0.0;
+    if (gnorm == 0.0) {
+        if (iters) *iters = 0;
+        if (rel_res) *rel_res = 0.0;
+        return TDBEM_OK;
+    }
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), e(m + 1), y(m), hv(2 * GM_MAXV);
+    for (;;) {
+        // V_0 = (g - A x) / beta
+        if ((s = tdbem_hessenberg_apply(A, x, w, stream))) return s;
+        CUDA_TRY(cudaMemcpyAsync(V, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        const double one = 1.0;
+        if ((s = upload(&one, 1))) return s;
+        launch_multi_axpy(w, n, 1, sd, -1.0, V, n, st);
+        double b2 = 0.0;
+        if ((s = dot(V, 1, V, &b2))) return s;
+        const double beta = sqrt(b2);
+        rr = beta / gnorm;
+        if (rr <= tol || total >= max_iter) break;
+        if ((s = upload(&beta, 1))) return s;
+        launch_scale_copy(V, sd, V, n, st);
+        std::fill(e.begin(), e.end(), 0.0);
+        e[0] = beta;
+        int jdone = 0;
+        bool stop = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
+            if ((s = tdbem_hessenberg_apply(A, vj, w, stream))) return s;
+            // w -= V h, twice (classical Gram-Schmidt with reorthogonalisation)
+            for (int pass = 0; pass < 2; ++pass) {
+                if ((s = dot(V, j + 1, w, hv.data() + pass * GM_MAXV))) return s;
+                launch_multi_axpy(V, n, j + 1, hd, -1.0, w, n, st);
+            }
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv[GM_MAXV + i];
+            double w2 = 0.0;
+            if ((s = dot(w, 1, w, &w2))) return s;
+            const double hn = sqrt(w2);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) {
+                if ((s = upload(&hn, 1))) return s;
+                launch_scale_copy(w, sd, vn, n, st);
+            }
+            // previous rotations, then a new one that zeroes H[j+1][j]
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+            const double rho = hypot(a, b);
+            cs[j] = rho > 0.0 ? a / rho : 1.0;
+            sn[j] = rho > 0.0 ? b / rho : 0.0;
+            H[(size_t)j * m + j] = rho;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            e[j + 1] = -sn[j] * e[j];
+            e[j] = cs[j] * e[j];
+            ++total;
+            jdone = j + 1;
+            rr = fabs(e[j + 1]) / gnorm;
+            if (rr <= tol || total >= max_iter || hn == 0.0) {
+                stop = true;
+                break;
+            }
+        }
+        // x += V y with R y = e (back substitution)
+        for (int i = jdone - 1; i >= 0; --i) {
+            double v = e[i];
+            for (int k = i + 1; k < jdone; ++k) v -= H[(size_t)i * m + k] * y[k];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? v / H[(size_t)i * m + i] : 0.0;
+        }
+        if ((s = upload(y.data(), jdone))) return s;
+        launch_multi_axpy(V, n, jdone, sd, 1.0, x, n, st);
+        CUDA_TRY(cudaGetLastError());
+        if (stop) {
+            // true residual of the final iterate
+            if ((s = tdbem_hessenberg_apply(A, x, w, stream))) return s;
+            CUDA_TRY(cudaMemcpyAsync(V, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            if ((s = upload(&one, 1))) return s;
+            launch_multi_axpy(w, n, 1, sd, -1.0, V, n, st);
+            if ((s = dot(V, 1, V, &b2))) return s;
+            rr = sqrt(b2) / gnorm;
+            break;
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = rr;
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
     if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = A->stats;

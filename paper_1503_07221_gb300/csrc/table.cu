@@ -155,4 +155,67 @@ void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStre
     psi_dct_kernel<<<(n + 127) / 128, 128, 0, st>>>(samples, total_sub, coef);
 }
 
+// ---- right-hand side g_k(l) = int_0^T int_Gamma g(x,t) phi_l(x) bdot_k(t) ----
+// (the vector of the linear system, Sec. 3). Neumann data by kind (with the
+// time grid scaled by the wave speed c, the data are taken at t = s / c):
+//   RHS_PLANE_WAVE  u_inc = exp(-(t - x.d - c0)^2 / (2 w^2)), p = (d, c0, w):
+//                   g = -du_inc/dn = (d.n) f'(t - x.d)  (sound-hard scatterer)
+//   RHS_SPHERE_N0   g = Y_0^0 sin(3t) t^2 e^{-t}           (Sec. 6.1)
+//   RHS_SPHERE_N1   g = Y_1^0(x) sin(2 pi t) t^3 e^{-2t}   (Sec. 6.1)
+__device__ static double rhs_data(int kind, const double *prm, const double *x, const double *n, double t) {
+    if (kind == RHS_PLANE_WAVE) {
+        const double s = t - (x[0] * prm[0] + x[1] * prm[1] + x[2] * prm[2]) - prm[3];
+        const double w = prm[4];
+        const double fp = -s / (w * w) * exp(-0.5 * (s / w) * (s / w));
+        return (n[0] * prm[0] + n[1] * prm[1] + n[2] * prm[2]) * fp;
+    }
+    if (t <= 0.0) return 0.0;
+    if (kind == RHS_SPHERE_N0) return 0.28209479177387814 * sin(3.0 * t) * t * t * exp(-t);  // Y_0^0 = 1/sqrt(4 pi)
+    return 0.48860251190291992 * x[2] * sin(2.0 * M_PI * t) * t * t * t * exp(-2.0 * t);     // Y_1^0 = sqrt(3/(4 pi)) z
+}
+
+// One thread per (time index k, vertex l): the triangles around l, 7 points
+// each, and the support of bdot_k split at every grid point into `sub`
+// panels of gn Gauss-Legendre points (FP64).
+__global__ void rhs_kernel(Geo g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+                           const double *gx, const double *gw, int gn, int sub, int kind, RhsParams prm,
+                           double *out) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= (int64_t)N * g.M) return;
+    const int k = (int)(id / g.M);
+    const int64_t l = id % g.M;
+    const int j0 = k == 0 ? 0 : k - 1, j1 = k == N - 1 ? N - 1 : k + 1;  // support [t_j0, t_j1]
+    double acc = 0.0;
+    for (int64_t q = g.vt_ptr[l]; q < g.vt_ptr[l + 1]; ++q) {
+        const int64_t e = g.vt_tri[q];
+        const int a = g.F[3 * e] == l ? 0 : (g.F[3 * e + 1] == l ? 1 : 2);
+        const double *geo = g.geo64 + 16 * e;  // n(3), area
+        for (int p = 0; p < 7; ++p) {
+            double x[3];
+            for (int d = 0; d < 3; ++d) x[d] = g.cen[3 * e + d] + g.dq[(e * 7 + p) * 3 + d];
+            double it = 0.0;
+            for (int j = j0; j < j1; ++j) {
+                const double h = (t[j + 1] - t[j]) / sub;
+                for (int sb = 0; sb < sub; ++sb)
+                    for (int m = 0; m < gn; ++m) {
+                        const double s = t[j] + (sb + gx[m]) * h;
+                        double b[3];
+                        basis(t, N, k, s, b);
+                        it += gw[m] * h * b[1] * rhs_data(kind, prm.p, x, geo, s / c);
+                    }
+            }
+            acc += geo[3] * rule_w[p] * rule_l[3 * p + a] * it;
+        }
+    }
+    out[id] = acc;
+}
+
+void launch_rhs(const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+                const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
+                cudaStream_t st) {
+    const int64_t n = (int64_t)N * g.M;
+    rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, t, N, c, rule_w, rule_l, gx, gw, gn, sub, kind, prm,
+                                                          out);
+}
+
 }  // namespace tdbem

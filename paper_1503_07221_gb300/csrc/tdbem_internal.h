@@ -205,6 +205,23 @@ size_t hessenberg_smem(int N);
 // transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
                               int64_t M, int N, int nsm, cudaStream_t st);
+// table.cu: right-hand side of the linear system (Neumann data by kind)
+enum { RHS_PLANE_WAVE = 0, RHS_SPHERE_N0 = 1, RHS_SPHERE_N1 = 2 };
+struct RhsParams {
+    double p[5];
+};
+void launch_rhs(const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+                const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
+                cudaStream_t st);
+// solve.cu: vector kernels of the GMRES solver
+void launch_multi_dot(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial, double *h,
+                      cudaStream_t st);
+void launch_multi_axpy(const double *V, int64_t ld, int nv, const double *h, double sign, double *w, int64_t n,
+                       cudaStream_t st);
+void launch_scale_copy(const double *w, const double *beta, double *v, int64_t n, cudaStream_t st);
+constexpr int GM_BLOCKS = 256;   // blocks of the dot-product partial sums
+constexpr int GM_MAXV = 64;      // most vectors in one multi_dot / multi_axpy
+
 // noalloc.cu: fixed scratch of MV_STATIC_MAX doubles for the matvec that
 // allocates nothing; its address on the current device
 constexpr int64_t MV_STATIC_MAX = (int64_t)1 << 21;

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtdbem.so")
 
 OK = 0
+RHS_PLANE_WAVE, RHS_SPHERE_N0, RHS_SPHERE_N1 = 0, 1, 2
 E_INVALID_ARG, E_MESH, E_TIMEGRID, E_OOM, E_CUDA, E_DEVICE, E_NOT_ASSEMBLED, E_UNSUPPORTED = range(1, 9)
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -68,6 +69,8 @@ def lib():
     L.tdbem_block_csr_host.argtypes = [vp, i64, i32, vp, vp, vp]
     L.tdbem_hessenberg_apply.argtypes = [vp, vp, vp, vp]
     L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
+    L.tdbem_rhs_assemble.argtypes = [vp, i32, vp, i32, vp, vp]
+    L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
     L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
     L.tdbem_mesh_destroy.argtypes = [vp]
     L.tdbem_timegrid_destroy.argtypes = [vp]
@@ -239,6 +242,27 @@ class Assembler:
         fn = lib().tdbem_hessenberg_apply_noalloc if noalloc else lib().tdbem_hessenberg_apply
         _check(fn(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(_stream(stream))))
         return y
+
+    def rhs(self, kind, params=(), out=None, stream=None):
+        """Right-hand side g_k(l) as a float64 CUDA tensor of shape (N, M)."""
+        import torch
+        shape = (self.grid.N, self.mesh.M)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _check(lib().tdbem_rhs_assemble(self.h, kind, p.ctypes.data if p.size else None, p.size,
+                                        C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
+        return out
+
+    def solve(self, g, restart=50, tol=1e-10, max_iter=2000, stream=None):
+        """alpha with A alpha = g by restarted GMRES on the device; returns
+        (alpha, iterations, relative residual)."""
+        import torch
+        alpha = torch.empty_like(g)
+        it, rr = C.c_int32(), C.c_double()
+        _check(lib().tdbem_solve_gmres(self.h, C.c_void_p(g.data_ptr()), C.c_void_p(alpha.data_ptr()), restart, tol,
+                                       max_iter, C.byref(it), C.byref(rr), C.c_void_p(_stream(stream))))
+        return alpha, it.value, rr.value
 
     def stats(self):
         s = Stats()
