@@ -16,9 +16,10 @@
 // nonzero by shuffle); shorter runs map lanes to nonzeros and reduce across
 // the warp. FP64 path: x, products and sums in FP64. Mixed path (FP32 far
 // values): x is rounded to FP32 in the transpose, far products are FP32 and
-// summed in FP32 over at most 32 products, and these partial sums are added
-// in FP64 (the FP64 pipe runs at 1/64 of the FP32 rate on this part); the
-// FP64 near values multiply the same x in FP64. Every y entry is written by
+// summed in FP32 over at most 32 products, and these partial sums are
+// accumulated as FP32 pairs with an error-free two-sum and added into the
+// FP64 row once per row and block (the FP64 pipe runs at 1/64 of the FP32
+// rate here); the FP64 near values multiply the same x in FP64. Every y entry is written by
 // its owning warp only, in a fixed order: the result is deterministic and
 // needs no atomics.
 #include <type_traits>
@@ -41,21 +42,49 @@ __global__ void __launch_bounds__(1024) transpose_kernel(const double *__restric
     if (j0 + ty < M && i0 + tx < N) xT[(j0 + ty) * N + i0 + tx] = (XT)tile[tx][ty];
 }
 
+// Accumulators of the sums over a row: FP64 in the FP64 path; in the mixed
+// path an unevaluated FP32 pair (hi, lo) updated with an error-free two-sum,
+// so the FP64 pipe (1/64 of the FP32 rate) is used once per row and block.
+struct AccPair {
+    float h, l;
+};
+__device__ __forceinline__ void acc_zero(double &a) { a = 0.0; }
+__device__ __forceinline__ void acc_zero(AccPair &a) { a.h = 0.f; a.l = 0.f; }
+__device__ __forceinline__ void acc_add(double &a, double v) { a += v; }
+__device__ __forceinline__ void acc_add(AccPair &a, float v) {
+    const float s = a.h + v;
+    const float bb = s - a.h;
+    a.l += (a.h - (s - bb)) + (v - bb);
+    a.h = s;
+}
+__device__ __forceinline__ void acc_add(AccPair &a, AccPair v) {
+    acc_add(a, v.h);
+    a.l += v.l;
+}
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(AccPair a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ AccPair shfl_xor(AccPair v, int o) {
+    return AccPair{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+
 // products and sums of one CSR row of one block for the positions of its run.
 // F32: FP32 products of FP32 values and FP32 x, partial sums of at most 32
-// products in FP32, added into FP64; otherwise FP64 products and sums.
+// products in FP32, accumulated as FP32 pairs (two-sum) and added into the
+// FP64 row once; otherwise FP64 products and sums.
 template <typename VT, typename XT, bool F32>
 __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                           const VT *__restrict__ val, int64_t l, int k0, int i0, int cnt,
                                           const XT *__restrict__ xT, int N, double *ys, int lane) {
     typedef typename std::conditional<F32, float, double>::type AT;
+    typedef typename std::conditional<F32, AccPair, double>::type ACC;
     const int64_t a = rp[l], e = rp[l + 1];
     if (a == e) return;
     if (cnt >= 16) {
         for (int p0 = 0; p0 < cnt; p0 += 32 * MV_PP) {
-            double acc[MV_PP];
+            ACC acc[MV_PP];
 #pragma unroll
-            for (int m = 0; m < MV_PP; ++m) acc[m] = 0.0;
+            for (int m = 0; m < MV_PP; ++m) acc_zero(acc[m]);
             const int pl = p0 + lane;
             for (int64_t base = a; base < e; base += 32) {
                 const int n = (int)min((int64_t)32, e - base);
@@ -74,25 +103,26 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
                         if (pl + 32 * m < cnt) part[m] = fma(v, (AT)xr[32 * m], part[m]);
                 }
 #pragma unroll
-                for (int m = 0; m < MV_PP; ++m) acc[m] += (double)part[m];
+                for (int m = 0; m < MV_PP; ++m) acc_add(acc[m], part[m]);
             }
 #pragma unroll
             for (int m = 0; m < MV_PP; ++m)
-                if (pl + 32 * m < cnt) ys[k0 + pl + 32 * m] += acc[m];
+                if (pl + 32 * m < cnt) ys[k0 + pl + 32 * m] += acc_value(acc[m]);
         }
     } else {
         for (int p = 0; p < cnt; ++p) {
-            double acc = 0.0;
+            ACC acc;
+            acc_zero(acc);
             for (int64_t c0 = a; c0 < e; c0 += 32 * 32) {
                 const int64_t c1 = min(e, c0 + 32 * 32);
                 AT part = 0;
                 for (int64_t nz = c0 + lane; nz < c1; nz += 32)
                     part = fma((AT)val[nz], (AT)xT[(int64_t)col[nz] * N + i0 + p], part);
-                acc += (double)part;
+                acc_add(acc, part);
             }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) ys[k0 + p] += acc;
+            for (int o = 16; o > 0; o >>= 1) acc_add(acc, shfl_xor(acc, o));
+            if (lane == 0) ys[k0 + p] += acc_value(acc);
         }
     }
     __syncwarp();
@@ -133,7 +163,7 @@ static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *
     transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, N, M);
     const size_t smem = hessenberg_smem(N);
     const int64_t ctas = (M + MV_WARPS - 1) / MV_WARPS;
-    const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 8);
+    const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 16);
     cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
