@@ -115,6 +115,7 @@ typedef struct {
     double ms_near;          /* near-field quadrature */
     double ms_extract;       /* CSR extraction */
     int64_t kernel_launches; /* kernels launched by the last tdbem_assemble_all */
+    int64_t graph_replays;   /* assemblies replayed from the recorded CUDA graph */
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */
@@ -157,8 +158,13 @@ TDBEM_API tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *
                               int32_t *m2, int32_t *m1, int64_t *nnz_far, int64_t *nnz_near);
 
 /* Assemble every unique block: psi tables, element-pair bounds, vertex-pair
- * windows, far and near quadrature, CSR extraction. Synchronises the stream
- * at the end and returns TDBEM_E_DEVICE if a kernel flagged an inconsistency. */
+ * windows, far and near quadrature, CSR extraction. The first call runs the
+ * steps with the host work between them (table copy, CSR sizes and
+ * allocation); later calls on the same assembler record the whole device
+ * sequence once into a CUDA graph (on an internal stream) and replay it on
+ * `stream`, every step recomputed, the CSR arrays and borrowed pointers
+ * unchanged. Synchronises the stream at the end and returns TDBEM_E_DEVICE if
+ * a kernel flagged an inconsistency or the pattern sizes changed. */
 TDBEM_API tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
 
 /* CSR of unique block b (borrowed device pointers). which = TDBEM_FAR: M+1

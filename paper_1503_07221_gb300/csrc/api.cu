@@ -396,6 +396,18 @@ struct tdbem_asm {
     // block-Hessenberg matvec: run descriptors and the transposed-x scratch
     DevBuf mv_blk, mv_xT;
     std::vector<MvBlock> mv_host;
+    // repeated assemblies: the recorded device sequence (CUDA graph)
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};  // the four timed phases
+    bool use_graph = true;
+    ~tdbem_asm() {
+        for (auto &g : gexec)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 static int kind_of(int64_t i, int64_t N) { return i == 0 ? 0 : (i == N - 1 ? 2 : 1); }  // F, I, L
@@ -752,17 +764,38 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
     return TDBEM_OK;
 }
 
-tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
-    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
-    cudaStream_t st = (cudaStream_t)stream;
+// The whole device sequence of one assembly. Eager (capture == false): with
+// the host steps between its parts (FP32 copy of the psi coefficients, CSR
+// sizes, allocation and offsets, status word, statistics). capture == true:
+// the device work only, to be recorded into a CUDA graph; everything the host
+// computed is then known from the eager run (same mesh and time grid give the
+// same tables, pattern and sizes).
+static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     const tdbem_mesh &m = *A->mesh;
     const int64_t M = m.M, E = m.E;
     const size_t MM = (size_t)M * M;
     const size_t rs = A->fp64 ? 8 : 4;
     const size_t nb = A->blocks.size();
-    cudaEvent_t ev[6];
-    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
-    CUDA_TRY(cudaEventRecord(ev[0], st));
+    (void)MM;
+    for (auto &e : A->ev)
+        if (!e) CUDA_TRY(cudaEventCreate(&e));
+    cudaEvent_t *ev = A->ev;
+    // phase boundaries: timing events when eager; when capturing, each phase
+    // becomes its own graph so the replay can put timing events between them
+    auto mark = [&](int k) -> cudaError_t {
+        if (!capture) return cudaEventRecord(ev[k], st);
+        cudaError_t e = cudaSuccess;
+        if (k > 0) {
+            cudaGraph_t gr = nullptr;
+            e = cudaStreamEndCapture(st, &gr);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&A->gexec[k - 1], gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return e;
+        }
+        if (k < 4) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        return e;
+    };
+    CUDA_TRY(mark(0));
     CUDA_TRY(cudaMemsetAsync(A->status.p, 0, 16, st));
     CUDA_TRY(cudaMemsetAsync(A->dense.p, 0, A->dense.n, st));
     CUDA_TRY(cudaMemsetAsync(A->dense_spec.p, 0, A->dense_spec.n, st));
@@ -780,7 +813,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
                        (double *)A->tab_samples.p + (size_t)n1 * NCHEB * 2, st);
     launch_psi_dct((const double *)A->tab_samples.p + (size_t)n1 * NCHEB * 2, n4, (double *)A->tab_coef4.p, st);
     CUDA_TRY(cudaGetLastError());
-    {
+    if (!capture) {
         std::vector<double> c1((size_t)n1 * NCHEB * 2);
         CUDA_TRY(cudaMemcpyAsync(c1.data(), A->tab_coef1.p, c1.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -803,7 +836,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         launch_count_quad(g, (const PairRec *)A->rec.p, npp, (int64_t *)A->quad_partial.p, 1024, st);
     }
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventRecord(ev[1], st));
+    CUDA_TRY(mark(1));
     // ---- far field, one launch per colour
     int dev = 0, nsm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -841,7 +874,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         }
     }
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventRecord(ev[2], st));
+    CUDA_TRY(mark(2));
     // ---- near field, one launch per colour
     for (size_t c = 0; c + 1 < A->color_off.size(); ++c) {
         NearArgs na;
@@ -869,7 +902,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
         }
     }
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventRecord(ev[3], st));
+    CUDA_TRY(mark(3));
     // ---- CSR: row counts, offsets, sizes, fill
     launch_row_counts2(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
                        (const int *)A->cls_dlo_d.p, (const int *)A->cls_dhi_d.p, (const int *)A->blk_of_lag_d.p,
@@ -878,6 +911,23 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     launch_scan_rows((const int64_t *)A->cnt_far.p, M, (int)nb, (int64_t *)A->rp_far.p, (int64_t *)A->tot_far.p, st);
     launch_scan_rows((const int64_t *)A->cnt_near.p, M, (int)nb, (int64_t *)A->rp_near.p, (int64_t *)A->tot_near.p, st);
     CUDA_TRY(cudaGetLastError());
+    if (capture) {
+        // sizes, buffers and offsets are those of the eager run
+        launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
+                    (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
+                    (const int *)A->blk_of_spec_d.p, nullptr, nullptr, (const int64_t *)A->rp_far.p,
+                    (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, (const double *)A->dense.p,
+                    (const double *)A->dense_spec.p, A->val_far.p, A->KW, 0, A->fp64, st);
+        launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
+                    (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
+                    (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
+                    (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
+                    (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true,
+                    st);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(mark(4));
+        return TDBEM_OK;
+    }
     A->nnz_far.assign(nb, 0);
     A->nnz_near.assign(nb, 0);
     std::vector<int64_t> qp(1024);
@@ -916,13 +966,12 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
                 (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
                 (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
     CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaEventRecord(ev[4], st));
+    CUDA_TRY(mark(4));
     int status = 0;
     CUDA_TRY(cudaMemcpyAsync(&status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     float ms[4];
     for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]));
-    for (auto &e : ev) cudaEventDestroy(e);
     A->stats.n_blocks = (int64_t)nb;
     A->stats.nnz = A->off_far[nb];
     A->stats.nnz_near = A->off_near[nb];
@@ -949,6 +998,57 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     if ((s = plan_matvec(*A, st))) return s;
     A->assembled = true;
     return TDBEM_OK;
+}
+
+// Replay of the recorded assembly graph on `st`, then the checks the eager
+// run makes on the host: status word and the per-block sizes (which the
+// unchanged pattern must reproduce), and the phase times from the events.
+static tdbem_status assemble_replay(tdbem_asm *A, cudaStream_t st) {
+    const size_t nb = A->blocks.size();
+    if (!A->gexec[3]) {
+        if (!A->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&A->cap_stream, cudaStreamNonBlocking));
+        const tdbem_status s = assemble_body(A, A->cap_stream, true);
+        if (s) {
+            cudaStreamCaptureStatus cs;
+            if (cudaStreamIsCapturing(A->cap_stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t gr = nullptr;
+                cudaStreamEndCapture(A->cap_stream, &gr);
+                if (gr) cudaGraphDestroy(gr);
+            }
+            for (auto &g : A->gexec)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+            return s;
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        CUDA_TRY(cudaEventRecord(A->ev[k], st));
+        CUDA_TRY(cudaGraphLaunch(A->gexec[k], st));
+    }
+    CUDA_TRY(cudaEventRecord(A->ev[4], st));
+    std::vector<int64_t> tf(nb), tn(nb);
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(tf.data(), A->tot_far.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(tn.data(), A->tot_near.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
+    if (tf != A->nnz_far || tn != A->nnz_near) return fail(TDBEM_E_DEVICE, "pattern sizes changed between assemblies");
+    float ms[4];
+    for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&ms[k], A->ev[k], A->ev[k + 1]));
+    A->stats.ms_pattern = ms[0];
+    A->stats.ms_far = ms[1];
+    A->stats.ms_near = ms[2];
+    A->stats.ms_extract = ms[3];
+    A->stats.ms_total = ms[0] + ms[1] + ms[2] + ms[3];
+    A->stats.graph_replays += 1;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
+    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (A->assembled && A->use_graph) return assemble_replay(A, st);
+    return assemble_body(A, st, false);
 }
 
 tdbem_status tdbem_block_csr(const tdbem_asm *A, int64_t b, int32_t which, const int64_t **rp, const int32_t **col,

@@ -39,7 +39,8 @@ class Stats(C.Structure):
     _fields_ = [("n_blocks", C.c_int64), ("nnz", C.c_int64), ("nnz_near", C.c_int64),
                 ("far_pairs", C.c_int64), ("near_pairs", C.c_int64), ("quad_points", C.c_int64),
                 ("ms_total", C.c_double), ("ms_pattern", C.c_double), ("ms_far", C.c_double),
-                ("ms_near", C.c_double), ("ms_extract", C.c_double), ("kernel_launches", C.c_int64)]
+                ("ms_near", C.c_double), ("ms_extract", C.c_double), ("kernel_launches", C.c_int64),
+                ("graph_replays", C.c_int64)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -110,3 +110,25 @@ def test_too_coarse_mesh_is_rejected(td):
     with pytest.raises(td.TdbemError) as e:
         td.Assembler(td.Mesh(V, F), td.TimeGrid(inputs.equidistant_grid(33, 2.0)))
     assert e.value.code == 8
+
+
+def test_graph_replay_is_identical(td):
+    """The second assembly replays the recorded CUDA graph: same values, bit
+    for bit, and the same borrowed pointers."""
+    V, F = inputs.icosphere(2)
+    t = inputs.equidistant_grid(17, 6.4)
+    for prec in (0, 1):
+        asm = td.Assembler(td.Mesh(V, F), td.TimeGrid(t), precision=prec)
+        asm.assemble()
+        first = [asm.block_csr_host(b, w) for b in range(asm.num_blocks()) for w in (td.FAR, td.NEAR)]
+        ptrs = [asm.block_csr_device(b, td.FAR) for b in range(asm.num_blocks())]
+        s1 = asm.stats()
+        for _ in range(2):
+            asm.assemble()
+        s2 = asm.stats()
+        assert s2["graph_replays"] == 2 and s1["graph_replays"] == 0
+        again = [asm.block_csr_host(b, w) for b in range(asm.num_blocks()) for w in (td.FAR, td.NEAR)]
+        for (r1, c1, v1), (r2, c2, v2) in zip(first, again):
+            assert np.array_equal(r1, r2) and np.array_equal(c1, c2) and np.array_equal(v1, v2)
+        assert ptrs == [asm.block_csr_device(b, td.FAR) for b in range(asm.num_blocks())]
+        assert s2["nnz"] == s1["nnz"] and s2["ms_far"] > 0
