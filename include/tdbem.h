@@ -116,6 +116,7 @@ typedef struct {
     double ms_extract;       /* CSR extraction */
     int64_t kernel_launches; /* kernels launched by the last tdbem_assemble_all */
     int64_t graph_replays;   /* assemblies replayed from the recorded CUDA graph */
+    int64_t matvec_variant;  /* matvec launch shape chosen by the autotuner (-1: not tuned yet) */
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */

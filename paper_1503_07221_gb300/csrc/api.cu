@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <set>
 #include <string>
@@ -396,6 +397,7 @@ struct tdbem_asm {
     // block-Hessenberg matvec: run descriptors and the transposed-x scratch
     DevBuf mv_blk, mv_xT;
     std::vector<MvBlock> mv_host;
+    mutable int mv_variant = -1;  // matvec launch shape chosen by the autotuner
     // repeated assemblies: the recorded device sequence (CUDA graph)
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaStream_t cap_stream = nullptr;
@@ -1089,6 +1091,56 @@ tdbem_status tdbem_block_csr_host(const tdbem_asm *A, int64_t b, int32_t which, 
     return TDBEM_OK;
 }
 
+// Matvec autotuner: on the first product of an assembler, time every launch
+// shape on the caller's x and y (one warm-up and one timed run each, CUDA
+// events) and keep the fastest; the choice is cached for the process per
+// (device, M, N, unique blocks, precision, nnz). The last run leaves y = A x
+// from the chosen shape, which the caller's launch then recomputes.
+static std::mutex g_mv_mu;
+static std::map<std::vector<int64_t>, int> g_mv_best;
+
+static tdbem_status tune_matvec(const tdbem_asm *A, const double *x, double *y, int nsm, cudaStream_t st) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    const int64_t N = A->tg->N, M = A->mesh->M;
+    const std::vector<int64_t> key = {dev, M, N, (int64_t)A->blocks.size(), A->fp64 ? 1 : 0, A->stats.nnz};
+    {
+        std::lock_guard<std::mutex> lock(g_mv_mu);
+        auto it = g_mv_best.find(key);
+        if (it != g_mv_best.end()) {
+            A->mv_variant = it->second;
+            return TDBEM_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    int best = 0;
+    float bt = 1e30f;
+    tdbem_status s = TDBEM_OK;
+    for (int v = 0; v < MV_NVARIANTS && !s; ++v) {
+        float ms = 0.f;
+        cudaError_t e = launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x,
+                                          (double *)A->mv_xT.p, y, M, (int)N, nsm, v, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess)
+            e = launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x,
+                                  (double *)A->mv_xT.p, y, M, (int)N, nsm, v, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) s = fail(TDBEM_E_CUDA, std::string("matvec autotuner: ") + cudaGetErrorString(e));
+        else if (ms < bt) { bt = ms; best = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    A->mv_variant = best;
+    std::lock_guard<std::mutex> lock(g_mv_mu);
+    g_mv_best[key] = best;
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
@@ -1100,8 +1152,12 @@ tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double 
     int dev = 0, nsm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (A->mv_variant < 0) {
+        tdbem_status ts = tune_matvec(A, x, y, nsm, st);
+        if (ts) return ts;
+    }
     CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, (double *)A->mv_xT.p, y,
-                               M, (int)N, nsm, st));
+                               M, (int)N, nsm, A->mv_variant, st));
     return TDBEM_OK;
 }
 
@@ -1120,8 +1176,9 @@ tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x,
     int dev = 0, nsm = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // the shape the autotuner chose for this assembler, if any (no timing here)
     CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, xT, y, M, (int)N,
-                               nsm, (cudaStream_t)stream));
+                               nsm, A->mv_variant < 0 ? 0 : A->mv_variant, (cudaStream_t)stream));
     return TDBEM_OK;
 }
 
@@ -1282,6 +1339,7 @@ tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, i
 tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
     if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = A->stats;
+    out->matvec_variant = A->mv_variant;
     return TDBEM_OK;
 }
 

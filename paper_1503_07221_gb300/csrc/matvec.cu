@@ -28,8 +28,8 @@
 
 namespace tdbem {
 
-constexpr int MV_WARPS = 8;
-constexpr int MV_PP = 4;  // positions per lane in one pass of the wide mapping
+// launch shape (positions per lane in one pass of the wide mapping, warps
+// per CTA) is a template parameter chosen by the autotuner (MV_VARIANTS)
 
 template <typename XT>
 __global__ void __launch_bounds__(1024) transpose_kernel(const double *__restrict__ x, XT *__restrict__ xT, int64_t N,
@@ -72,7 +72,7 @@ __device__ __forceinline__ AccPair shfl_xor(AccPair v, int o) {
 // F32: FP32 products of FP32 values and FP32 x, partial sums of at most 32
 // products in FP32, accumulated as FP32 pairs (two-sum) and added into the
 // FP64 row once; otherwise FP64 products and sums.
-template <typename VT, typename XT, bool F32>
+template <typename VT, typename XT, bool F32, int PP>
 __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                           const VT *__restrict__ val, int64_t l, int k0, int i0, int cnt,
                                           const XT *__restrict__ xT, int N, double *ys, int lane) {
@@ -81,32 +81,32 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
     const int64_t a = rp[l], e = rp[l + 1];
     if (a == e) return;
     if (cnt >= 16) {
-        for (int p0 = 0; p0 < cnt; p0 += 32 * MV_PP) {
-            ACC acc[MV_PP];
+        for (int p0 = 0; p0 < cnt; p0 += 32 * PP) {
+            ACC acc[PP];
 #pragma unroll
-            for (int m = 0; m < MV_PP; ++m) acc_zero(acc[m]);
+            for (int m = 0; m < PP; ++m) acc_zero(acc[m]);
             const int pl = p0 + lane;
             for (int64_t base = a; base < e; base += 32) {
                 const int n = (int)min((int64_t)32, e - base);
                 int cj = 0;
                 AT cv = 0;
                 if (lane < n) { cj = col[base + lane]; cv = (AT)val[base + lane]; }
-                AT part[MV_PP];
+                AT part[PP];
 #pragma unroll
-                for (int m = 0; m < MV_PP; ++m) part[m] = 0;
+                for (int m = 0; m < PP; ++m) part[m] = 0;
                 for (int t = 0; t < n; ++t) {
                     const int j = __shfl_sync(0xffffffffu, cj, t);
                     const AT v = __shfl_sync(0xffffffffu, cv, t);
                     const XT *xr = xT + (int64_t)j * N + i0 + pl;
 #pragma unroll
-                    for (int m = 0; m < MV_PP; ++m)
+                    for (int m = 0; m < PP; ++m)
                         if (pl + 32 * m < cnt) part[m] = fma(v, (AT)xr[32 * m], part[m]);
                 }
 #pragma unroll
-                for (int m = 0; m < MV_PP; ++m) acc_add(acc[m], part[m]);
+                for (int m = 0; m < PP; ++m) acc_add(acc[m], part[m]);
             }
 #pragma unroll
-            for (int m = 0; m < MV_PP; ++m)
+            for (int m = 0; m < PP; ++m)
                 if (pl + 32 * m < cnt) ys[k0 + pl + 32 * m] += acc_value(acc[m]);
         }
     } else {
@@ -131,50 +131,65 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
 // VT: far value type. F32 (mixed path): x in FP32, far products in FP32 with
 // FP64 sums of 32-product partials; the FP64 near values multiply the same
 // FP32 x in FP64. Otherwise (FP64 path) everything is FP64.
-template <typename VT, bool F32>
-__global__ void __launch_bounds__(MV_WARPS * 32) hessenberg_kernel(const MvBlock *__restrict__ blk, int nb,
-                                                                   const void *__restrict__ xT_,
-                                                                   double *__restrict__ y, int64_t M, int N) {
+template <typename VT, bool F32, int PP, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *__restrict__ blk, int nb,
+                                                                const void *__restrict__ xT_,
+                                                                double *__restrict__ y, int64_t M, int N) {
     typedef typename std::conditional<F32, float, double>::type XT;
     const XT *xT = (const XT *)xT_;
     extern __shared__ double ys_all[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *ys = ys_all + (size_t)w * N;
-    for (int64_t l = (int64_t)blockIdx.x * MV_WARPS + w; l < M; l += (int64_t)gridDim.x * MV_WARPS) {
+    for (int64_t l = (int64_t)blockIdx.x * WARPS + w; l < M; l += (int64_t)gridDim.x * WARPS) {
         for (int k = lane; k < N; k += 32) ys[k] = 0.0;
         __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const MvBlock B = blk[b];
-            row_apply<VT, XT, F32>(B.rp_far, B.col_far, (const VT *)B.val_far, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
-            row_apply<double, XT, false>(B.rp_near, B.col_near, B.val_near, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
+            row_apply<VT, XT, F32, PP>(B.rp_far, B.col_far, (const VT *)B.val_far, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
+            row_apply<double, XT, false, PP>(B.rp_near, B.col_near, B.val_near, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
         }
         for (int k = lane; k < N; k += 32) y[(int64_t)k * M + l] = ys[k];
         __syncwarp();
     }
 }
 
-size_t hessenberg_smem(int N) { return (size_t)MV_WARPS * N * sizeof(double); }
+// The tunable launch shapes: (positions per lane, warps per CTA).
+static const int MV_VARIANTS[MV_NVARIANTS][2] = {{4, 8}, {2, 8}, {8, 8}, {4, 4}, {2, 4}, {8, 4}};
 
-template <typename VT, bool F32>
-static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *xT, double *y, int64_t M, int N,
-                             int nsm, cudaStream_t st) {
-    typedef typename std::conditional<F32, float, double>::type XT;
-    const dim3 tg((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
-    transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, N, M);
-    const size_t smem = hessenberg_smem(N);
-    const int64_t ctas = (M + MV_WARPS - 1) / MV_WARPS;
+template <typename VT, bool F32, int PP, int WARPS>
+static cudaError_t launch_mv_shape(const MvBlock *blk, int nb, const void *xT, double *y, int64_t M, int N, int nsm,
+                                   cudaStream_t st) {
+    const size_t smem = (size_t)WARPS * N * sizeof(double);
+    const int64_t ctas = (M + WARPS - 1) / WARPS;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 16);
-    cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32, PP, WARPS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    hessenberg_kernel<VT, F32><<<grid, MV_WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
+    hessenberg_kernel<VT, F32, PP, WARPS><<<grid, WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
     return cudaGetLastError();
 }
 
+template <typename VT, bool F32>
+static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *xT, double *y, int64_t M, int N,
+                             int nsm, int variant, cudaStream_t st) {
+    typedef typename std::conditional<F32, float, double>::type XT;
+    const dim3 tg((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
+    transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, N, M);
+    switch (variant) {
+        case 1: return launch_mv_shape<VT, F32, 2, 8>(blk, nb, xT, y, M, N, nsm, st);
+        case 2: return launch_mv_shape<VT, F32, 8, 8>(blk, nb, xT, y, M, N, nsm, st);
+        case 3: return launch_mv_shape<VT, F32, 4, 4>(blk, nb, xT, y, M, N, nsm, st);
+        case 4: return launch_mv_shape<VT, F32, 2, 4>(blk, nb, xT, y, M, N, nsm, st);
+        case 5: return launch_mv_shape<VT, F32, 8, 4>(blk, nb, xT, y, M, N, nsm, st);
+        default: return launch_mv_shape<VT, F32, 4, 8>(blk, nb, xT, y, M, N, nsm, st);
+    }
+}
+
+
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
-                              int64_t M, int N, int nsm, cudaStream_t st) {
-    if (far_fp64) return launch_mv<double, false>(blk, nb, x, xT, y, M, N, nsm, st);
-    return launch_mv<float, true>(blk, nb, x, xT, y, M, N, nsm, st);
+                              int64_t M, int N, int nsm, int variant, cudaStream_t st) {
+    if (far_fp64) return launch_mv<double, false>(blk, nb, x, xT, y, M, N, nsm, variant, st);
+    return launch_mv<float, true>(blk, nb, x, xT, y, M, N, nsm, variant, st);
 }
 
 }  // namespace tdbem

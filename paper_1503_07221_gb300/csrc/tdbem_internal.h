@@ -201,10 +201,11 @@ struct MvBlock {
     const double *val_near;
     int32_t k0, i0, cnt, pad;
 };
-size_t hessenberg_smem(int N);
 // transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
+// variant: one of MV_NVARIANTS launch shapes (0 = default), see matvec.cu
+constexpr int MV_NVARIANTS = 6;
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
-                              int64_t M, int N, int nsm, cudaStream_t st);
+                              int64_t M, int N, int nsm, int variant, cudaStream_t st);
 // table.cu: right-hand side of the linear system (Neumann data by kind)
 enum { RHS_PLANE_WAVE = 0, RHS_SPHERE_N0 = 1, RHS_SPHERE_N1 = 2 };
 struct RhsParams {

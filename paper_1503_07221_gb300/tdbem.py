@@ -40,7 +40,7 @@ class Stats(C.Structure):
                 ("far_pairs", C.c_int64), ("near_pairs", C.c_int64), ("quad_points", C.c_int64),
                 ("ms_total", C.c_double), ("ms_pattern", C.c_double), ("ms_far", C.c_double),
                 ("ms_near", C.c_double), ("ms_extract", C.c_double), ("kernel_launches", C.c_int64),
-                ("graph_replays", C.c_int64)]
+                ("graph_replays", C.c_int64), ("matvec_variant", C.c_int64)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
