@@ -108,7 +108,35 @@ struct Setup32 {
 // average away and the cancellation in the odd prototype would amplify. The
 // last three additions (n = 2, 1, 0) carry a Kahan compensation term.
 constexpr int NLOW = 8;
+// Low-order part of one directly evaluated panel j (terms n < NLOW, the
+// leading residuals, and the sum hj of the terms n >= NLOW).
+__device__ __forceinline__ f2 panel_low(const ChebF32 &C, int j, const f2 (&T)[NLOW], f2 hj) {
+    f2 a = 0ull;
+#pragma unroll
+    for (int n = 0; n < NCHEB_LO; ++n) a = fma2(lo2(C, j, n), T[n], a);
+    a = fma2(pk(1.f, 1.f), hj, a);
+#pragma unroll
+    for (int n = NLOW - 1; n >= 3; --n) a = fma2(coef2(C, j, n), T[n], a);
+    // the three largest terms with Kahan compensation: their partial sums
+    // are of the size of psi, and their FP32 roundings would otherwise
+    // dominate the error of the panel value
+    f2 y = mul2(coef2(C, j, 2), T[2]);
+    f2 t = add2(a, y);
+    f2 nc = sub2(y, sub2(t, a));  // minus the rounding error of t
+    a = t;
+    y = fma2(coef2(C, j, 1), T[1], nc);
+    t = add2(a, y);
+    nc = sub2(y, sub2(t, a));
+    return add2(t, add2(coef2(C, j, 0), nc));
+}
+
 __device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10]) {
+    // Evaluated directly: C1 (panels 0-2) and C3 (7-9), and the first two C2
+    // panels (3, 4) with their even and odd terms kept apart. The inner
+    // prototype is antisymmetric about the centre of its support (Eq.
+    // symmetryXi, p = 0), so C2 panel 3 - s at x is minus panel s at -x:
+    // O_s(x) - E_s(x). Two of the ten Chebyshev sums are thereby saved.
+    constexpr int DIR[6] = {0, 1, 2, 7, 8, 9};
     f2 T[NLOW];
     float t0 = 1.f, t1 = x;
     const float x2 = x + x;
@@ -121,9 +149,11 @@ __device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10
         t1 = tn;
         T[n] = pk(tn, tn);
     }
-    f2 hi[10];
+    f2 hi[6], hE[2], hO[2];
 #pragma unroll
-    for (int j = 0; j < 10; ++j) hi[j] = 0ull;
+    for (int d = 0; d < 6; ++d) hi[d] = 0ull;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) { hE[q] = 0ull; hO[q] = 0ull; }
 #pragma unroll
     for (int n = NLOW; n < NCHEB; ++n) {
         const float tn = x2 * t1 - t0;
@@ -131,28 +161,38 @@ __device__ __forceinline__ void lag_panels(const ChebF32 &C, float x, f2 (&v)[10
         t1 = tn;
         const f2 tt = pk(tn, tn);
 #pragma unroll
-        for (int j = 0; j < 10; ++j) hi[j] = fma2(coef2(C, j, n), tt, hi[j]);
+        for (int d = 0; d < 6; ++d) hi[d] = fma2(coef2(C, DIR[d], n), tt, hi[d]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (n & 1) hO[q] = fma2(coef2(C, 3 + q, n), tt, hO[q]);
+            else hE[q] = fma2(coef2(C, 3 + q, n), tt, hE[q]);
+        }
     }
 #pragma unroll
-    for (int j = 0; j < 10; ++j) {
-        f2 a = 0ull;
+    for (int d = 0; d < 6; ++d) v[DIR[d]] = panel_low(C, DIR[d], T, hi[d]);
 #pragma unroll
-        for (int n = 0; n < NCHEB_LO; ++n) a = fma2(lo2(C, j, n), T[n], a);
-        a = fma2(pk(1.f, 1.f), hi[j], a);
-#pragma unroll
-        for (int n = NLOW - 1; n >= 3; --n) a = fma2(coef2(C, j, n), T[n], a);
-        // the three largest terms with Kahan compensation: their partial sums
-        // are of the size of psi, and their FP32 roundings would otherwise
-        // dominate the error of the panel value
+    for (int q = 0; q < 2; ++q) {
+        const int j = 3 + q;
+        f2 aE = fma2(lo2(C, j, 2), T[2], mul2(lo2(C, j, 0), T[0]));
+        f2 aO = fma2(lo2(C, j, 3), T[3], mul2(lo2(C, j, 1), T[1]));
+        aE = add2(aE, hE[q]);
+        aO = add2(aO, hO[q]);
+        aO = fma2(coef2(C, j, 7), T[7], aO);
+        aE = fma2(coef2(C, j, 6), T[6], aE);
+        aO = fma2(coef2(C, j, 5), T[5], aO);
+        aE = fma2(coef2(C, j, 4), T[4], aE);
+        aO = fma2(coef2(C, j, 3), T[3], aO);
+        // Kahan compensation of the largest terms, as in panel_low
         f2 y = mul2(coef2(C, j, 2), T[2]);
-        f2 t = add2(a, y);
-        f2 nc = sub2(y, sub2(t, a));  // minus the rounding error of t
-        a = t;
-        y = fma2(coef2(C, j, 1), T[1], nc);
-        t = add2(a, y);
-        nc = sub2(y, sub2(t, a));
-        a = add2(t, add2(coef2(C, j, 0), nc));
-        v[j] = a;
+        f2 t = add2(aE, y);
+        f2 nc = sub2(y, sub2(t, aE));
+        aE = add2(t, add2(coef2(C, j, 0), nc));
+        y = mul2(coef2(C, j, 1), T[1]);
+        t = add2(aO, y);
+        nc = sub2(y, sub2(t, aO));
+        aO = add2(t, nc);
+        v[j] = add2(aE, aO);
+        v[6 - q] = sub2(aO, aE);
     }
 }
 
@@ -390,8 +430,9 @@ __device__ __forceinline__ void scatter_staged(const FarArgs &A, const Setup32 &
         const int wlo = swlo[it], whi = swhi[it];
         double *dst = A.dense + (c * MM + (int64_t)su.Ft[a] * M + A.chunk_vert[v0 + v]) * KW;
         const double *cur = stg + (size_t)it * KW;
-        // the vertex's triangles in this chunk, up to 8 per batch, in registers
-        constexpr int MAXS = 8;
+        // the vertex's triangles in this chunk, 3 per batch, in registers (a batch of
+        // 3 keeps the predicated sums short; most vertices need one or two)
+        constexpr int MAXS = 3;
         for (int x0 = s0; x0 < s1; x0 += MAXS) {
             int lbi[MAXS], off[MAXS];
             bool has[MAXS];
