@@ -252,7 +252,10 @@ def run_ours(args):
     flops = far_flops(st)
     achieved = flops / (far_avg_ms * 1e-3) / 1e12
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    peak = sm_count * 128 * 2 * 2.070e9 / 1e12
+    peak_nominal = sm_count * 128 * 2 * 2.070e9 / 1e12
+    # measured right after the timed region, at the clock the GPU runs at now
+    peak32, peak64 = tdbem.measure_fma_peaks()
+    peak = peak32
     clocks = clk.summary()
     fp64_cmp = None
     if args.fp64_compare and prec == tdbem.PREC_MIXED:
@@ -261,6 +264,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         a64 = tdbem.Assembler(mesh, grid, precision=tdbem.PREC_FP64)
         a64.assemble()
+        a64.hessenberg_apply(X[0], Y)  # first product tunes the launch shape, untimed
         torch.cuda.synchronize()
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
@@ -303,8 +307,12 @@ def run_ours(args):
             "matvec_nnz_reuse_per_s": mv_work * world / (mv_ms * 1e-3) if args.matvecs else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "far_kernel (FP32 FMA pipe)",
-                         "peak_basis": "%d SMs x 128 FP32 FMA/clk x 2 x 2070 MHz max clock" % sm_count},
+                         "kernel": "far32_kernel (FP32 FMA pipe)",
+                         "peak_basis": "measured: packed FP32 FMA microbenchmark (tdbem_measure_fma_peaks) "
+                                       "after the timed region",
+                         "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
+                         "nominal_basis": "%d SMs x 128 FP32 FMA/clk x 2 x 2070 MHz max clock" % sm_count,
+                         "fp64_fma_peak_measured": peak64},
             "e2e": e2e, "clocks": clocks, "gpu_launches": launches_per_step * args.steps,
             "fp64_gpu": fp64_cmp, "cpu_baseline": cpu,
         }

@@ -250,6 +250,14 @@ TDBEM_API tdbem_status tdbem_solve_gmres(const tdbem_asm *a, const double *g_dev
                                          int32_t restart, double tol, int32_t max_iter, int32_t *iters,
                                          double *rel_res, void *stream);
 
+/* Measured FMA throughput of the current device in TFLOP/s (an FMA counts
+ * two flops): packed FP32 pairs (the far kernel's arithmetic) and FP64. Not
+ * part of the paper's method: the denominators of the roofline fractions,
+ * taken at the clock the device runs at when called. Runs two short kernels
+ * (tens of ms), allocates nothing, synchronises the stream. Either output
+ * may be NULL. */
+TDBEM_API tdbem_status tdbem_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops, void *stream);
+
 /* Assembly counters and the per-phase device times of the last assembly. */
 TDBEM_API tdbem_status tdbem_stats(const tdbem_asm *a, tdbem_stats_t *out);
 

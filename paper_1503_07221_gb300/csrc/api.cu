@@ -1336,6 +1336,11 @@ tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, i
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops, void *stream) {
+    CUDA_TRY(measure_fma_peaks(fp32_tflops, fp64_tflops, (cudaStream_t)stream));
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
     if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = A->stats;

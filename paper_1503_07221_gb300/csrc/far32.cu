@@ -359,6 +359,16 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
     if (lane == 0) { su.tau = tau; su.ch = ch; su.Ft[0] = Ft0; su.Ft[1] = Ft1; su.Ft[2] = Ft2; }
 }
 
+// a + b for FP32 pairs: two-sum of the high parts, renormalised
+__device__ __forceinline__ FF ff_plus(FF a, FF b) {
+    const float s = a.h + b.h;
+    const float bb = s - a.h;
+    const float e = (a.h - (s - bb)) + (b.h - bb);
+    const float l = (a.l + b.l) + e;
+    const float h = s + l;
+    return FF{h, l - (h - s)};
+}
+
 // Staging of the current chunk's scatter inputs, issued by the producer warp
 // while the compute warps run the quadrature: the lag-window bounds of every
 // (trial vertex, test corner, class) item and the window values themselves
@@ -428,8 +438,11 @@ __device__ __forceinline__ void scatter_staged(const FarArgs &A, const Setup32 &
         const int rho = A.lt.rho[c];
         const int so = c == C1 ? slot0<OFF>(C1) : c == C2 ? slot0<OFF>(C2) : slot0<OFF>(C3);
         const int wlo = swlo[it], whi = swhi[it];
-        double *dst = A.dense + (c * MM + (int64_t)su.Ft[a] * M + A.chunk_vert[v0 + v]) * KW;
-        const double *cur = stg + (size_t)it * KW;
+        // the mixed path keeps its far lag windows as FP32 pairs (hi, lo):
+        // updated with two-sums on the FP32 pipe, exact enough for the FP64
+        // sums they stand for, and no FP64 add on this critical phase
+        FF *dst = reinterpret_cast<FF *>(A.dense) + (c * MM + (int64_t)su.Ft[a] * M + A.chunk_vert[v0 + v]) * KW;
+        const FF *cur = reinterpret_cast<const FF *>(stg) + (size_t)it * KW;
         // the vertex's triangles in this chunk, 3 per batch, in registers (a batch of
         // 3 keeps the predicated sums short; most vertices need one or two)
         constexpr int MAXS = 3;
@@ -464,8 +477,8 @@ __device__ __forceinline__ void scatter_staged(const FarArgs &A, const Setup32 &
                 }
                 // first batch adds to the staged value, later ones to what the
                 // previous batch stored
-                const double base_v = x0 == s0 ? cur[d - wlo] : dst[d - wlo];
-                dst[d - wlo] = base_v + lb_value(sum);
+                const FF base_v = x0 == s0 ? cur[d - wlo] : dst[d - wlo];
+                dst[d - wlo] = ff_plus(base_v, sum);
             }
         }
     }

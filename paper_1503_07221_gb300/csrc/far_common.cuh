@@ -60,7 +60,7 @@ __device__ __forceinline__ R rule_l(const FarArgs &A, int k) {
 // [32 sigma][NS slots][9] values; su the element-pair setup of the chunk.
 // Lb element types: float or double values, or FP32 pairs (hi, lo) summed
 // with an error-free two-sum
-struct FF {
+struct alignas(8) FF {
     float h, l;
 };
 __device__ __forceinline__ void lb_add(float &s, float v) { s += v; }

@@ -4,6 +4,8 @@
 // assembled values into per-block CSR.
 #include <math.h>
 
+#include <type_traits>
+
 #include "tdbem_internal.h"
 
 namespace tdbem {
@@ -382,7 +384,13 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                                         __popc(bal & lt_mask);
                     col[pos] = (int32_t)j;
                     const int64_t src = nearp ? ((c * M + l) * NB + (k - k0)) : (c * MM + l * M + j);
-                    val[pos] = (T)dense[src * KW + (d - a)];
+                    if constexpr (std::is_same<T, float>::value) {
+                        // mixed far windows hold FP32 pairs (hi, lo)
+                        const float2 pr = reinterpret_cast<const float2 *>(dense)[src * KW + (d - a)];
+                        val[pos] = pr.x + pr.y;
+                    } else {
+                        val[pos] = (T)dense[src * KW + (d - a)];
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) cur[w][x] += __popc(bal);

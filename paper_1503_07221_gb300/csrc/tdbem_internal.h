@@ -223,6 +223,8 @@ void launch_scale_copy(const double *w, const double *beta, double *v, int64_t n
 constexpr int GM_BLOCKS = 256;   // blocks of the dot-product partial sums
 constexpr int GM_MAXV = 64;      // most vectors in one multi_dot / multi_axpy
 
+// peaks.cu: FMA throughput of the device (roofline denominators)
+cudaError_t measure_fma_peaks(double *fp32, double *fp64, cudaStream_t st);
 // noalloc.cu: fixed scratch of MV_STATIC_MAX doubles for the matvec that
 // allocates nothing; its address on the current device
 constexpr int64_t MV_STATIC_MAX = (int64_t)1 << 21;

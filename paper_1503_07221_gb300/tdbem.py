@@ -72,6 +72,7 @@ def lib():
     L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.tdbem_rhs_assemble.argtypes = [vp, i32, vp, i32, vp, vp]
     L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
+    L.tdbem_measure_fma_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
     L.tdbem_mesh_destroy.argtypes = [vp]
     L.tdbem_timegrid_destroy.argtypes = [vp]
@@ -125,6 +126,13 @@ def _stream(stream):
         import torch
         return torch.cuda.current_stream().cuda_stream
     return int(stream)
+
+
+def measure_fma_peaks(stream=None):
+    """(FP32 packed-FMA, FP64 FMA) throughput of the current device, TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib().tdbem_measure_fma_peaks(C.byref(a), C.byref(b), C.c_void_p(_stream(stream))))
+    return a.value, b.value
 
 
 class Mesh:

@@ -132,3 +132,10 @@ def test_graph_replay_is_identical(td):
             assert np.array_equal(r1, r2) and np.array_equal(c1, c2) and np.array_equal(v1, v2)
         assert ptrs == [asm.block_csr_device(b, td.FAR) for b in range(asm.num_blocks())]
         assert s2["nnz"] == s1["nnz"] and s2["ms_far"] > 0
+
+
+def test_measured_fma_peaks(td):
+    """The roofline denominators: packed FP32 and FP64 FMA throughput."""
+    p32, p64 = td.measure_fma_peaks()
+    print("FMA peaks: fp32 %.1f TFLOP/s, fp64 %.2f TFLOP/s" % (p32, p64))
+    assert 10.0 < p32 < 200.0 and 0.05 < p64 < 100.0
