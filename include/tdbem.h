@@ -250,6 +250,48 @@ TDBEM_API tdbem_status tdbem_solve_gmres(const tdbem_asm *a, const double *g_dev
                                          int32_t restart, double tol, int32_t max_iter, int32_t *iters,
                                          double *rel_res, void *stream);
 
+/* Solve A alpha = g by flexible GMRES FGMRES(restart, levels(inner...)) with
+ * the recursive algebraic block-Hessenberg preconditioner (Sec. 4.2,
+ * Algorithm 1; the notation of the solver tables of Sec. 6).
+ * Preconditioner: on a diagonal range of block rows/columns [lo, hi) split at
+ * h = lo + ceil((hi - lo) / 2), M equals A without the block (h - 1, h)
+ * above the diagonal (0-based), and M^-1 r = (M11^-1 r1, M22^-1 (r2 -
+ * M21 M11^-1 r1)). The two diagonal systems of a level-l splitting are
+ * solved approximately by one FGMRES cycle of inner_iters[l - 1] steps from
+ * zero with the same relative tolerance, preconditioned by the level-(l + 1)
+ * splitting of that half while l < levels and the half spans two blocks or
+ * more; the last level is unpreconditioned. levels = 0 runs the same
+ * iteration without a preconditioner (GMRES(restart)).
+ * g and alpha: caller-owned device arrays of N*M doubles, not overlapping;
+ * zero initial guess; stop when the residual estimate reaches tol ||g||, or
+ * when a restart finds the true residual there, or after max_iter outer
+ * iterations. *iters: outer iterations done; *rel_res: the true relative
+ * residual ||g - A alpha|| / ||g|| of the result (either may be NULL).
+ * inner_iters: host array of `levels` counts, each 1..62 (NULL when levels
+ * is 0). The Krylov bases of all levels (about (2 restart + 3) N M doubles
+ * plus (2 inner_l + 3) N M / 2^l at level l) are allocated through the
+ * registered allocator for the call. The preconditioner application is
+ * recorded once per call as a CUDA graph on an internal stream and replayed
+ * on `stream` at every outer step; the host reads one small status record
+ * per outer step. Synchronises the stream. TDBEM_E_NOT_ASSEMBLED before an
+ * assembly; TDBEM_E_INVALID_ARG for restart outside 1..62, tol outside
+ * (0, 1), max_iter < 1, levels outside 0..24, an inner count outside 1..62,
+ * NULL or overlapping arrays; TDBEM_E_OOM if the bases cannot be allocated. */
+TDBEM_API tdbem_status tdbem_solve_fgmres(const tdbem_asm *a, const double *g_dev, double *alpha_dev,
+                                          int32_t restart, double tol, int32_t max_iter, int32_t levels,
+                                          const int32_t *inner_iters, int32_t *iters, double *rel_res,
+                                          void *stream);
+
+/* z = M^-1 r: one application of the recursive preconditioner of
+ * tdbem_solve_fgmres (levels >= 1 levels, inner_iters as there, tol the
+ * relative tolerance of the inner solves). r and z: caller-owned device
+ * arrays of N*M doubles, not overlapping. Workspace as for
+ * tdbem_solve_fgmres with restart 1, allocated for the call. Launched
+ * directly (no graph); synchronises the stream. Errors as for
+ * tdbem_solve_fgmres, and TDBEM_E_INVALID_ARG for levels < 1. */
+TDBEM_API tdbem_status tdbem_precond_apply(const tdbem_asm *a, int32_t levels, const int32_t *inner_iters,
+                                           double tol, const double *r_dev, double *z_dev, void *stream);
+
 /* Measured FMA throughput of the current device in TFLOP/s (an FMA counts
  * two flops): packed FP32 pairs (the far kernel's arithmetic) and FP64. Not
  * part of the paper's method: the denominators of the roofline fractions,

@@ -1336,6 +1336,83 @@ tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, i
     return TDBEM_OK;
 }
 
+// shared checks and set-up of tdbem_solve_fgmres and tdbem_precond_apply:
+// validates the arguments, tunes the product if needed (on x, y), fills the
+// solver plan and allocates its workspace
+static tdbem_status krylov_setup(const tdbem_asm *A, int32_t restart, double tol, int32_t levels,
+                                 const int32_t *inner, const double *x, double *y, KrylovSolver &K, DevBuf &ws,
+                                 cudaStream_t st) {
+    if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    if (restart < 1 || restart > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "restart must be in 1..62");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(TDBEM_E_INVALID_ARG, "tol must be in (0, 1)");
+    if (levels < 0 || levels > KR_MAXLEVELS) return fail(TDBEM_E_INVALID_ARG, "levels must be in 0..24");
+    if (levels > 0 && !inner) return fail(TDBEM_E_INVALID_ARG, "inner_iters is NULL");
+    for (int l = 0; l < levels; ++l)
+        if (inner[l] < 1 || inner[l] > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "inner iterations must be in 1..62");
+    const int64_t N = A->tg->N, M = A->mesh->M;
+    const size_t bytes = (size_t)(N * M) * sizeof(double);
+    const char *xb = (const char *)x, *yb = (const char *)y;
+    if (xb < yb + bytes && yb < xb + bytes) return fail(TDBEM_E_INVALID_ARG, "arrays overlap");
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (A->mv_variant < 0) {
+        tdbem_status ts = tune_matvec(A, x, y, nsm, st);
+        if (ts) return ts;
+    }
+    K.op = MvOp{(const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, (double *)A->mv_xT.p, M, (int)N, nsm,
+                A->mv_variant};
+    K.levels = levels;
+    K.m[0] = restart;
+    for (int l = 1; l <= levels; ++l) K.m[l] = inner[l - 1];
+    K.tol = tol;
+    size_t need = 0;
+    K.layout(nullptr, &need);
+    tdbem_status s = dev_alloc(ws, need, st);
+    if (s) return s;
+    CUDA_TRY(cudaMemsetAsync(ws.p, 0, need, st));
+    K.layout(ws.p, &need);
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_solve_fgmres(const tdbem_asm *A, const double *g, double *x, int32_t restart, double tol,
+                                int32_t max_iter, int32_t levels, const int32_t *inner_iters, int32_t *iters,
+                                double *rel_res, void *stream) {
+    if (max_iter < 1) return fail(TDBEM_E_INVALID_ARG, "max_iter must be >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    KrylovSolver K;
+    DevBuf ws;
+    tdbem_status s = krylov_setup(A, restart, tol, levels, inner_iters, g, x, K, ws, st);
+    if (s) return s;
+    cudaStream_t cap = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    int it = 0;
+    double rr = 0.0;
+    const cudaError_t e = K.solve(g, x, max_iter, st, cap, &it, &rr);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return fail(TDBEM_E_CUDA, std::string("FGMRES: ") + cudaGetErrorString(e));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (iters) *iters = it;
+    if (rel_res) *rel_res = rr;
+    return TDBEM_OK;
+}
+
+tdbem_status tdbem_precond_apply(const tdbem_asm *A, int32_t levels, const int32_t *inner_iters, double tol,
+                                 const double *r, double *z, void *stream) {
+    if (levels < 1) return fail(TDBEM_E_INVALID_ARG, "levels must be in 1..24");
+    cudaStream_t st = (cudaStream_t)stream;
+    KrylovSolver K;
+    DevBuf ws;
+    tdbem_status s = krylov_setup(A, 1, tol, levels, inner_iters, r, z, K, ws, st);
+    if (s) return s;
+    const cudaError_t e = K.apply_preconditioner(r, z, st);
+    if (e != cudaSuccess) return fail(TDBEM_E_CUDA, std::string("preconditioner: ") + cudaGetErrorString(e));
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_measure_fma_peaks(double *fp32_tflops, double *fp64_tflops, void *stream) {
     CUDA_TRY(measure_fma_peaks(fp32_tflops, fp64_tflops, (cudaStream_t)stream));
     return TDBEM_OK;

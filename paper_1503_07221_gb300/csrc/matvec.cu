@@ -33,7 +33,8 @@ namespace tdbem {
 
 template <typename XT>
 __global__ void __launch_bounds__(1024) transpose_kernel(const double *__restrict__ x, XT *__restrict__ xT, int64_t N,
-                                                         int64_t M) {
+                                                         int64_t M, const int *__restrict__ active) {
+    if (active && !*active) return;
     __shared__ double tile[32][33];
     const int64_t j0 = (int64_t)blockIdx.x * 32, i0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
@@ -131,24 +132,37 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
 // VT: far value type. F32 (mixed path): x in FP32, far products in FP32 with
 // FP64 sums of 32-product partials; the FP64 near values multiply the same
 // FP32 x in FP64. Otherwise (FP64 path) everything is FP64.
+//
+// Block ranges: only block rows ka <= k < ka + nk and block columns
+// ia <= i < ia + nx take part (the diagonal and off-diagonal parts of the
+// splitting of Sec. 4.2); x is then (nx, M) and y (nk, M). The whole product
+// is ka = ia = 0, nk = nx = N. Each run is cut to the positions p with both
+// k0 + p and i0 + p inside the ranges. active: if given and zero, the
+// kernel does nothing (a converged solve, see fgmres.cu).
 template <typename VT, bool F32, int PP, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *__restrict__ blk, int nb,
                                                                 const void *__restrict__ xT_,
-                                                                double *__restrict__ y, int64_t M, int N) {
+                                                                double *__restrict__ y, int64_t M, int ka, int nk,
+                                                                int ia, int nx, const int *__restrict__ active) {
     typedef typename std::conditional<F32, float, double>::type XT;
+    if (active && !*active) return;
     const XT *xT = (const XT *)xT_;
     extern __shared__ double ys_all[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double *ys = ys_all + (size_t)w * N;
+    double *ys = ys_all + (size_t)w * nk;
     for (int64_t l = (int64_t)blockIdx.x * WARPS + w; l < M; l += (int64_t)gridDim.x * WARPS) {
-        for (int k = lane; k < N; k += 32) ys[k] = 0.0;
+        for (int k = lane; k < nk; k += 32) ys[k] = 0.0;
         __syncwarp();
         for (int b = 0; b < nb; ++b) {
             const MvBlock B = blk[b];
-            row_apply<VT, XT, F32, PP>(B.rp_far, B.col_far, (const VT *)B.val_far, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
-            row_apply<double, XT, false, PP>(B.rp_near, B.col_near, B.val_near, l, B.k0, B.i0, B.cnt, xT, N, ys, lane);
+            const int plo = max(0, max(ka - B.k0, ia - B.i0));
+            const int phi = min(B.cnt, min(ka + nk - B.k0, ia + nx - B.i0));
+            if (phi <= plo) continue;
+            const int k0 = B.k0 + plo - ka, i0 = B.i0 + plo - ia, cnt = phi - plo;
+            row_apply<VT, XT, F32, PP>(B.rp_far, B.col_far, (const VT *)B.val_far, l, k0, i0, cnt, xT, nx, ys, lane);
+            row_apply<double, XT, false, PP>(B.rp_near, B.col_near, B.val_near, l, k0, i0, cnt, xT, nx, ys, lane);
         }
-        for (int k = lane; k < N; k += 32) y[(int64_t)k * M + l] = ys[k];
+        for (int k = lane; k < nk; k += 32) y[(int64_t)k * M + l] = ys[k];
         __syncwarp();
     }
 }
@@ -157,39 +171,44 @@ __global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *_
 static const int MV_VARIANTS[MV_NVARIANTS][2] = {{4, 8}, {2, 8}, {8, 8}, {4, 4}, {2, 4}, {8, 4}};
 
 template <typename VT, bool F32, int PP, int WARPS>
-static cudaError_t launch_mv_shape(const MvBlock *blk, int nb, const void *xT, double *y, int64_t M, int N, int nsm,
-                                   cudaStream_t st) {
-    const size_t smem = (size_t)WARPS * N * sizeof(double);
+static cudaError_t launch_mv_shape(const MvBlock *blk, int nb, const void *xT, double *y, int64_t M, int ka, int nk,
+                                   int ia, int nx, const int *active, int nsm, cudaStream_t st) {
+    const size_t smem = (size_t)WARPS * nk * sizeof(double);
     const int64_t ctas = (M + WARPS - 1) / WARPS;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 16);
     cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32, PP, WARPS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    hessenberg_kernel<VT, F32, PP, WARPS><<<grid, WARPS * 32, smem, st>>>(blk, nb, xT, y, M, N);
+    hessenberg_kernel<VT, F32, PP, WARPS><<<grid, WARPS * 32, smem, st>>>(blk, nb, xT, y, M, ka, nk, ia, nx, active);
     return cudaGetLastError();
 }
 
 template <typename VT, bool F32>
-static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *xT, double *y, int64_t M, int N,
-                             int nsm, int variant, cudaStream_t st) {
+static cudaError_t launch_mv(const MvBlock *blk, int nb, const double *x, void *xT, double *y, int64_t M, int ka,
+                             int nk, int ia, int nx, const int *active, int nsm, int variant, cudaStream_t st) {
     typedef typename std::conditional<F32, float, double>::type XT;
-    const dim3 tg((unsigned)((M + 31) / 32), (unsigned)((N + 31) / 32));
-    transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, N, M);
+    const dim3 tg((unsigned)((M + 31) / 32), (unsigned)((nx + 31) / 32));
+    transpose_kernel<XT><<<tg, dim3(32, 32), 0, st>>>(x, (XT *)xT, nx, M, active);
     switch (variant) {
-        case 1: return launch_mv_shape<VT, F32, 2, 8>(blk, nb, xT, y, M, N, nsm, st);
-        case 2: return launch_mv_shape<VT, F32, 8, 8>(blk, nb, xT, y, M, N, nsm, st);
-        case 3: return launch_mv_shape<VT, F32, 4, 4>(blk, nb, xT, y, M, N, nsm, st);
-        case 4: return launch_mv_shape<VT, F32, 2, 4>(blk, nb, xT, y, M, N, nsm, st);
-        case 5: return launch_mv_shape<VT, F32, 8, 4>(blk, nb, xT, y, M, N, nsm, st);
-        default: return launch_mv_shape<VT, F32, 4, 8>(blk, nb, xT, y, M, N, nsm, st);
+        case 1: return launch_mv_shape<VT, F32, 2, 8>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
+        case 2: return launch_mv_shape<VT, F32, 8, 8>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
+        case 3: return launch_mv_shape<VT, F32, 4, 4>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
+        case 4: return launch_mv_shape<VT, F32, 2, 4>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
+        case 5: return launch_mv_shape<VT, F32, 8, 4>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
+        default: return launch_mv_shape<VT, F32, 4, 8>(blk, nb, xT, y, M, ka, nk, ia, nx, active, nsm, st);
     }
 }
 
-
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
                               int64_t M, int N, int nsm, int variant, cudaStream_t st) {
-    if (far_fp64) return launch_mv<double, false>(blk, nb, x, xT, y, M, N, nsm, variant, st);
-    return launch_mv<float, true>(blk, nb, x, xT, y, M, N, nsm, variant, st);
+    return launch_hessenberg_range(blk, nb, far_fp64, x, xT, y, M, 0, N, 0, N, nullptr, nsm, variant, st);
+}
+
+cudaError_t launch_hessenberg_range(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
+                                    int64_t M, int ka, int nk, int ia, int nx, const int *active, int nsm, int variant,
+                                    cudaStream_t st) {
+    if (far_fp64) return launch_mv<double, false>(blk, nb, x, xT, y, M, ka, nk, ia, nx, active, nsm, variant, st);
+    return launch_mv<float, true>(blk, nb, x, xT, y, M, ka, nk, ia, nx, active, nsm, variant, st);
 }
 
 }  // namespace tdbem

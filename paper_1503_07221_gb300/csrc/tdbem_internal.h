@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -206,6 +207,11 @@ struct MvBlock {
 constexpr int MV_NVARIANTS = 6;
 cudaError_t launch_hessenberg(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
                               int64_t M, int N, int nsm, int variant, cudaStream_t st);
+// y (nk, M) = A[ka:ka+nk, ia:ia+nx] x (nx, M) over block rows and columns;
+// nothing happens when active is given and *active == 0 (device flag)
+cudaError_t launch_hessenberg_range(const MvBlock *blk, int nb, bool far_fp64, const double *x, double *xT, double *y,
+                                    int64_t M, int ka, int nk, int ia, int nx, const int *active, int nsm, int variant,
+                                    cudaStream_t st);
 // table.cu: right-hand side of the linear system (Neumann data by kind)
 enum { RHS_PLANE_WAVE = 0, RHS_SPHERE_N0 = 1, RHS_SPHERE_N1 = 2 };
 struct RhsParams {
@@ -216,12 +222,73 @@ void launch_rhs(const Geo &g, const double *t, int N, double c, const double *ru
                 cudaStream_t st);
 // solve.cu: vector kernels of the GMRES solver
 void launch_multi_dot(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial, double *h,
-                      cudaStream_t st);
+                      cudaStream_t st, const int *active = nullptr);
 void launch_multi_axpy(const double *V, int64_t ld, int nv, const double *h, double sign, double *w, int64_t n,
-                       cudaStream_t st);
+                       cudaStream_t st, const int *active = nullptr);
 void launch_scale_copy(const double *w, const double *beta, double *v, int64_t n, cudaStream_t st);
 constexpr int GM_BLOCKS = 256;   // blocks of the dot-product partial sums
 constexpr int GM_MAXV = 64;      // most vectors in one multi_dot / multi_axpy
+
+// fgmres.cu: flexible GMRES with the recursive block-Hessenberg
+// preconditioner (Sec. 4.2, Algorithm 1), iterated on the device
+constexpr int KR_MAXM = GM_MAXV - 2;  // most steps of one cycle
+constexpr int KR_MAXLEVELS = 24;      // most levels of the preconditioner
+// the status that the host reads after every outer step (the head of KState)
+struct KHead {
+    int run, stop, jdone, iters;
+    double resid;
+};
+// one solve's scalars: run = the cycle goes on; stop = it ended converged
+// (or at breakdown); resid = residual estimate / |b|; H row-major with row
+// stride KR_MAXM; hc = the two Gram-Schmidt passes of the current step
+struct KState {
+    int run, stop, jdone, iters;
+    double resid;
+    int m, pad;
+    double bref, inv, r2, w2;
+    double hc[2 * GM_MAXV];
+    double H[(KR_MAXM + 1) * KR_MAXM];
+    double cs[KR_MAXM], sn[KR_MAXM], e[KR_MAXM + 1], y[KR_MAXM];
+};
+static_assert(offsetof(KState, resid) == offsetof(KHead, resid), "KHead is the head of KState");
+// the block-Hessenberg product of one assembled matrix
+struct MvOp {
+    const MvBlock *blk;
+    int nb;
+    bool far_fp64;
+    double *xT;  // scratch of N M doubles
+    int64_t M;
+    int N, nsm, variant;
+};
+class KrylovSolver {
+  public:
+    MvOp op{};
+    int levels = 0;                   // preconditioner levels (0: none)
+    int m[KR_MAXLEVELS + 1] = {};     // m[0] restart length, m[l] steps at level l
+    double tol = 0.0;                 // relative tolerance, outer and inner
+    int64_t graph_nodes = 0;          // nodes of the recorded preconditioner
+    // sets the workspace pointers into ws (nullptr: only the size)
+    cudaError_t layout(void *ws, size_t *bytes);
+    // alpha with A alpha = g from zero; cap: a stream for graph capture
+    cudaError_t solve(const double *g, double *x, int max_iter, cudaStream_t st, cudaStream_t cap, int *iters,
+                      double *rel_res);
+    // z = M^-1 r, one application of the level-1 preconditioner
+    cudaError_t apply_preconditioner(const double *r, double *z, cudaStream_t st);
+
+  private:
+    int nblk[KR_MAXLEVELS + 1] = {};
+    KState *states = nullptr;
+    double *partial = nullptr, *pin = nullptr, *pout = nullptr;
+    double *V[KR_MAXLEVELS + 1] = {}, *Z[KR_MAXLEVELS + 1] = {}, *w[KR_MAXLEVELS + 1] = {},
+           *t[KR_MAXLEVELS + 1] = {};
+    cudaError_t matvec(const double *x, double *y, int ka, int nk, int ia, int nx, const int *active,
+                       cudaStream_t st);
+    cudaError_t arnoldi(int l, int lo, int hi, int j, const double *z, cudaStream_t st);
+    cudaError_t inner_solve(int l, int lo, int hi, const double *rhs, double *x, const int *parent, cudaStream_t st);
+    cudaError_t precondition(int l, int lo, int hi, const double *in, double *out, const int *parent,
+                             cudaStream_t st);
+    cudaError_t read_head(KHead *h, cudaStream_t st);
+};
 
 // peaks.cu: FMA throughput of the device (roofline denominators)
 cudaError_t measure_fma_peaks(double *fp32, double *fp64, cudaStream_t st);

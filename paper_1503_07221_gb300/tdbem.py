@@ -72,6 +72,9 @@ def lib():
     L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.tdbem_rhs_assemble.argtypes = [vp, i32, vp, i32, vp, vp]
     L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
+    L.tdbem_solve_fgmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, vp, C.POINTER(i32),
+                                     C.POINTER(C.c_double), vp]
+    L.tdbem_precond_apply.argtypes = [vp, i32, vp, C.c_double, vp, vp, vp]
     L.tdbem_measure_fma_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     L.tdbem_stats.argtypes = [vp, C.POINTER(Stats)]
     L.tdbem_mesh_destroy.argtypes = [vp]
@@ -272,6 +275,31 @@ class Assembler:
         _check(lib().tdbem_solve_gmres(self.h, C.c_void_p(g.data_ptr()), C.c_void_p(alpha.data_ptr()), restart, tol,
                                        max_iter, C.byref(it), C.byref(rr), C.c_void_p(_stream(stream))))
         return alpha, it.value, rr.value
+
+    def solve_fgmres(self, g, restart=50, tol=1e-5, max_iter=20000, inner=(10,), stream=None):
+        """alpha with A alpha = g by FGMRES(restart, len(inner)(inner...)) with
+        the recursive block-Hessenberg preconditioner (inner = (): no
+        preconditioner); returns (alpha, outer iterations, true relative
+        residual)."""
+        import torch
+        alpha = torch.empty_like(g)
+        inn = (C.c_int32 * max(1, len(inner)))(*inner)
+        it, rr = C.c_int32(), C.c_double()
+        _check(lib().tdbem_solve_fgmres(self.h, C.c_void_p(g.data_ptr()), C.c_void_p(alpha.data_ptr()), restart, tol,
+                                        max_iter, len(inner), inn if len(inner) else None, C.byref(it), C.byref(rr),
+                                        C.c_void_p(_stream(stream))))
+        return alpha, it.value, rr.value
+
+    def precondition(self, r, inner=(10,), tol=1e-5, out=None, stream=None):
+        """z = M^-1 r, one application of the recursive preconditioner with
+        len(inner) levels."""
+        import torch
+        z = torch.empty_like(r) if out is None else out
+        inn = (C.c_int32 * max(1, len(inner)))(*inner)
+        _check(lib().tdbem_precond_apply(self.h, len(inner), inn if len(inner) else None, tol,
+                                         C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()),
+                                         C.c_void_p(_stream(stream))))
+        return z
 
     def stats(self):
         s = Stats()
