@@ -144,11 +144,13 @@ def run_reference(args):
 
 
 def far_flops(st):
-    # algorithmic FP32 work of the far kernel per far point pair:
-    # T_n recurrence (31 FMA), 10 panels x (psi, psi~) x 33 coefficients
-    # (660 FMA), accumulation 10 panels x 4 (40 FMA), weights (3 FMA),
-    # distance correction (~12 FMA-equivalents): 746 FMA = 1492 FLOP
-    return 1492.0 * st["far_pairs"] * 49
+    # algorithmic FP32 work of the far kernel per far point pair: distance
+    # and Chebyshev argument (~14 FMA-equivalents), T_n recurrence (31 FMA),
+    # 8 evaluated panels x (psi, psi~) x 33 coefficients (528 FMA; the other
+    # two C2 panels follow from the antisymmetry of Eq. symmetryXi, 4 FMA-
+    # equivalents), weights (4 FMA), accumulation 10 panels x 4 (40 FMA):
+    # 621 FMA = 1242 FLOP. Compensation terms are not counted.
+    return 1242.0 * st["far_pairs"] * 49
 
 
 def run_ours(args):
