@@ -24,7 +24,11 @@
  * b = t_k - t_{i-2}, 1-based) starts at or beyond diam(Gamma). On an
  * equidistant grid only the blocks of Sec. 5.1 are assembled -- the first two
  * block columns, the last block row, A_{2,3} and A_{N-1,N} -- and every other
- * block is one of them by Eq. relationAtildeBlock. Within a block, entry
+ * block is one of them by Eq. relationAtildeBlock. On any other grid (for
+ * instance geometrically graded steps) the shift invariance is lost and
+ * every nonzero block (k,i), i <= k+1, is assembled from its own psi_{k,i}
+ * (Sec. 3, "O(N^2 p^2)" distinct functions); the list is k-major in both
+ * cases. Within a block, entry
  * (l,j) is structural iff the open support (a,b) meets [mindist_{l,j},
  * maxdist_{l,j}] (Eq. SparsitySmallBlock); such entries stay in the pattern
  * even where they evaluate to 0.
@@ -140,8 +144,11 @@ TDBEM_API tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, con
  * p: Legendre degree of the time basis (only 0 in this build); basis_kind: 0
  * = the paper's step f = erf(2 artanh x)/2 + 1/2; c: wave speed (> 0, r =
  * |x-y|/c). An equidistant grid (|t_i - i T/(N-1)| <= 1e-12 T) uses the
- * Toeplitz block reuse of Sec. 5.1 and needs N >= 5; other grids are not
- * supported by this build (TDBEM_E_UNSUPPORTED). */
+ * Toeplitz block reuse of Sec. 5.1; any other grid assembles every nonzero
+ * block on its own (the uneven steps enter the basis through the local step
+ * widths: b_1 uses t_1 - t_0, inner flanks the widths of their own
+ * intervals). The assembler needs 5 <= N <= 1000 and, on a non-equidistant
+ * grid, at most 256 nonzero blocks in one block column. */
 TDBEM_API tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t basis_kind,
                                    double c, tdbem_timegrid **out);
 
@@ -164,8 +171,12 @@ TDBEM_API tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *
  * allocation); later calls on the same assembler record the whole device
  * sequence once into a CUDA graph (on an internal stream) and replay it on
  * `stream`, every step recomputed, the CSR arrays and borrowed pointers
- * unchanged. Synchronises the stream at the end and returns TDBEM_E_DEVICE if
- * a kernel flagged an inconsistency or the pattern sizes changed. */
+ * unchanged. On a non-equidistant grid every call runs eagerly: the blocks
+ * are assembled in batches of block columns whose FP64 staging windows fit a
+ * quarter of the free device memory (at most 24 GiB), one far and one near
+ * launch per triangle colour and batch. Synchronises the stream at the end
+ * and returns TDBEM_E_DEVICE if a kernel flagged an inconsistency or the
+ * pattern sizes changed. */
 TDBEM_API tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
 
 /* CSR of unique block b (borrowed device pointers). which = TDBEM_FAR: M+1

@@ -403,7 +403,25 @@ struct tdbem_asm {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};  // the four timed phases
     bool use_graph = true;
+    // graded (non-equidistant) grids: every nonzero block is its own unique
+    // block; column-major block numbering, panels and batches (graded.cu)
+    bool graded = false;
+    std::vector<int> g_colblk, g_colk0, g_cb2api, g_pan0, g_p64, g_kw;
+    std::vector<double> g_ga, g_gb;
+    std::vector<GPan64> g_pan64;
+    std::vector<float4> g_pan32;
+    int g_npan = 0, g_nset64 = 0, g_maxpan = 0, g_njob32 = 0;
+    double g_smax = -1.0;  // window spread Dmax - Dmin the batches were planned for
+    std::vector<int> g_bi0, g_bi1;           // batches of trial columns [i0, i1)
+    std::vector<int64_t> g_doff, g_ndoff;    // per column: window offsets inside its batch
+    size_t g_dense_max = 0, g_ndense_max = 0;
+    DevBuf gpair, gvmin, gvmax, gpartial, g_ga_d, g_gb_d, g_colblk_d, g_colk0_d, g_cb2api_d, g_pan0_d, g_pan64_d,
+        g_pan32_d, g_p64_d, g_kw_d, g_doff_d, g_ndoff_d, g_tkb, g_tib, g_tr0, g_tdr, g_samples, g_coef, g_coef32,
+        g_geol, g_cenh, g_cenl, g_coloff_d, g_dense, g_ndense;
+    std::vector<cudaEvent_t> g_ev;
     ~tdbem_asm() {
+        for (auto &e : g_ev)
+            if (e) cudaEventDestroy(e);
         for (auto &g : gexec)
             if (g) cudaGraphExecDestroy(g);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -483,6 +501,198 @@ static tdbem_status plan_blocks(tdbem_asm &A) {
     return TDBEM_OK;
 }
 
+// Graded grid: every (k, i) with i <= k + 1 whose support (a, b) starts below
+// diam(Gamma) is assembled (Sec. 3.2; no reuse without shift invariance).
+// The caller's list is k-major like the equidistant one; internally the
+// blocks of each trial column i form a contiguous k-range (a and b grow with
+// k). psi_{k,i} is smooth between the breakpoints t_{k-a} - t_{i-b},
+// a, b in {0, 1, 2} (Sec. 3.1), which bound its Chebyshev panels.
+static tdbem_status plan_graded(tdbem_asm &A) {
+    const tdbem_timegrid &tg = *A.tg;
+    const int64_t N = tg.N;
+    const double *t = tg.t.data();
+    const double T = t[N - 1];
+    const double tie = 1e-12 * T;
+    auto tl = [&](int64_t q) { return q == 0 ? 0.0 : t[q - 1]; };
+    auto tr = [&](int64_t q) { return q == N - 1 ? T : t[q + 1]; };
+    A.blocks.clear();
+    std::vector<int> api_of((size_t)(N * N), -1);
+    for (int64_t k = 0; k < N; ++k)
+        for (int64_t i = 0; i < N && i <= k + 1; ++i) {
+            const double a = std::max(0.0, tl(k) - tr(i)), b = tr(k) - tl(i);
+            if (!(b > a) || a >= A.mesh->diam - tie) continue;
+            api_of[k * N + i] = (int)A.blocks.size();
+            A.blocks.push_back({(int)k, (int)i, -1, 0, a, b});
+        }
+    A.g_colblk.assign(N + 1, 0);
+    A.g_colk0.assign(N, 0);
+    A.g_cb2api.clear();
+    A.g_ga.clear();
+    A.g_gb.clear();
+    A.g_pan0.clear();
+    A.g_pan64.clear();
+    A.g_pan32.clear();
+    A.g_maxpan = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        A.g_colblk[i] = (int)A.g_cb2api.size();
+        int64_t kfirst = -1, klast = -2;
+        for (int64_t k = 0; k < N; ++k)
+            if (api_of[k * N + i] >= 0) {
+                if (kfirst < 0) kfirst = k;
+                else if (k != klast + 1) return fail(TDBEM_E_UNSUPPORTED, "non-contiguous block column");
+                klast = k;
+            }
+        A.g_colk0[i] = kfirst < 0 ? 0 : (int)kfirst;
+        if (klast - kfirst + 1 > GP_MAXK) return fail(TDBEM_E_UNSUPPORTED, "more than 256 blocks in one block column");
+        const int pcol0 = (int)A.g_pan64.size();
+        for (int64_t k = kfirst; kfirst >= 0 && k <= klast; ++k) {
+            const Block &B = A.blocks[api_of[k * N + i]];
+            A.g_cb2api.push_back(api_of[k * N + i]);
+            A.g_ga.push_back(B.a);
+            A.g_gb.push_back(B.b);
+            A.g_pan0.push_back((int)A.g_pan64.size());
+            const double X[3] = {tl(k), t[k], tr(k)}, Y[3] = {tl(i), t[i], tr(i)};
+            std::vector<double> br = {B.a, B.b};
+            for (double x : X)
+                for (double y : Y)
+                    if (x - y > B.a && x - y < B.b) br.push_back(x - y);
+            std::sort(br.begin(), br.end());
+            std::vector<double> m = {br[0]};
+            for (size_t q = 1; q < br.size(); ++q)
+                if (br[q] - m.back() > 1e-13 * T) m.push_back(br[q]);
+            if (m.back() != B.b) m.back() = B.b;
+            if (m.size() < 2 || m.size() - 1 > (size_t)GP_MAXPAN) return fail(TDBEM_E_UNSUPPORTED, "bad panel count");
+            for (size_t q = 0; q + 1 < m.size(); ++q) {
+                const double s = m[q], w = m[q + 1] - m[q], mid = s + 0.5 * w;
+                A.g_pan64.push_back({s, w, 0.0, 0.0});
+                const float mh = (float)mid;
+                A.g_pan32.push_back(make_float4((float)s, mh, (float)(mid - (double)mh), (float)(2.0 / w)));
+            }
+        }
+        A.g_maxpan = std::max(A.g_maxpan, (int)A.g_pan64.size() - pcol0);
+    }
+    A.g_colblk[N] = (int)A.g_cb2api.size();
+    A.g_pan0.push_back((int)A.g_pan64.size());
+    A.g_npan = (int)A.g_pan64.size();
+    // FP64 coefficient sets: S64 sub-panels per panel; the mixed path needs them
+    // only where near pairs (r <= the largest vertex star) evaluate psi
+    const double rnear = A.mesh->max_star * (1.0 + 1e-9) + tie;
+    A.g_p64.assign(A.g_npan, -1);
+    A.g_nset64 = 0;
+    for (int p = 0; p < A.g_npan; ++p) {
+        GPan64 &q = A.g_pan64[p];
+        q.z = A.S64 / q.y;
+        if (A.fp64 || q.x < rnear) { A.g_p64[p] = A.g_nset64; A.g_nset64 += A.S64; }
+    }
+    return TDBEM_OK;
+}
+
+// Longest window [K1, K2] of a vertex pair in column i when Dmax - Dmin <=
+// smax: with K1 = k (Dmin just below b_k), K2 is at most the last k' with
+// a_k' < b_k + smax.
+static int graded_kw(const tdbem_asm &A, int64_t i, double smax) {
+    const int c0 = A.g_colblk[i], nk = A.g_colblk[i + 1] - c0;
+    int best = 1;
+    for (int x = 0; x < nk; ++x) {
+        int y = x;
+        while (y + 1 < nk && A.g_ga[c0 + y + 1] < A.g_gb[c0 + x] + smax) ++y;
+        best = std::max(best, y - x + 1);
+    }
+    return best;
+}
+
+// Uploads and allocations of a graded-grid assembler (the time-grid and
+// geometry parts the equidistant path also uses, plus the graded block,
+// panel and table-job arrays). Window sizes and batches follow in the
+// first assembly, once the vertex-pair bounds are known.
+static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
+    A.graded = true;
+    A.use_graph = false;
+    A.S64 = 4;
+    tdbem_status s = plan_graded(A);
+    if (s) return s;
+    const tdbem_mesh &m = *A.mesh;
+    const int64_t M = m.M, E = m.E;
+    std::vector<int32_t> colors;
+    A.color_off.assign(1, 0);
+    for (auto &c : m.colors) { colors.insert(colors.end(), c.begin(), c.end()); A.color_off.push_back((int64_t)colors.size()); }
+    std::vector<float> geol(16 * E), cenh(3 * E), cenl(3 * E);
+    for (int64_t k = 0; k < 16 * E; ++k) geol[k] = (float)(m.geo64[k] - (double)m.geo32[k]);
+    for (int64_t k = 0; k < 3 * E; ++k) {
+        cenh[k] = (float)m.cen[k];
+        cenl[k] = (float)(m.cen[k] - (double)cenh[k]);
+    }
+    std::vector<double> rw64(7), rl64(21);
+    for (int k = 0; k < 7; ++k) { rw64[k] = m.rule_W[k]; for (int d = 0; d < 3; ++d) rl64[3 * k + d] = m.rule_L[k][d]; }
+    std::vector<double> gx, gw;
+    gauss_legendre01(24, gx, gw);
+    // psi table jobs: FP32 set (one per panel, mixed path), then the FP64 sets
+    std::vector<int> kb, ib;
+    std::vector<double> r0, dr;
+    const int ncb = (int)A.g_cb2api.size();
+    auto add_jobs = [&](bool fp64set) {
+        for (int cb = 0; cb < ncb; ++cb) {
+            const Block &B = A.blocks[A.g_cb2api[cb]];
+            for (int p = A.g_pan0[cb]; p < A.g_pan0[cb + 1]; ++p) {
+                const GPan64 &q = A.g_pan64[p];
+                if (!fp64set) { kb.push_back(B.kb); ib.push_back(B.ib); r0.push_back(q.x); dr.push_back(q.y); continue; }
+                if (A.g_p64[p] < 0) continue;
+                for (int sb = 0; sb < A.S64; ++sb) {
+                    kb.push_back(B.kb);
+                    ib.push_back(B.ib);
+                    r0.push_back(q.x + q.y * sb / A.S64);
+                    dr.push_back(q.y / A.S64);
+                }
+            }
+        }
+    };
+    if (!A.fp64) add_jobs(false);
+    const size_t njob32 = kb.size();
+    add_jobs(true);
+    if (kb.size() - njob32 != (size_t)A.g_nset64) return fail(TDBEM_E_UNSUPPORTED, "FP64 table job count");
+#define UPG(buf, vec) if ((s = upload(A.buf, vec, st))) return s
+    UPG(F, m.F); UPG(V, m.V); UPG(cen, m.cen); UPG(dq, m.dq); UPG(dq32, m.dq32); UPG(geo32, m.geo32);
+    UPG(geo64, m.geo64); UPG(vt_ptr, m.vt_ptr); UPG(vt_tri, m.vt_tri); UPG(adj_ptr, m.adj_ptr);
+    UPG(adj_tri, m.adj_tri); UPG(adj_perm, m.adj_perm); UPG(adj_nbr, m.adj_nbr); UPG(nbr_ptr, m.nbr_ptr);
+    UPG(nbr, m.nbr); UPG(colors, colors); UPG(tgrid, A.tg->t); UPG(rule_w64, rw64); UPG(rule_l64, rl64);
+    UPG(gl_x, gx); UPG(gl_w, gw); UPG(g_geol, geol); UPG(g_cenh, cenh); UPG(g_cenl, cenl);
+    UPG(g_coloff_d, A.color_off); UPG(g_ga_d, A.g_ga); UPG(g_gb_d, A.g_gb); UPG(g_colblk_d, A.g_colblk);
+    UPG(g_colk0_d, A.g_colk0); UPG(g_cb2api_d, A.g_cb2api); UPG(g_pan0_d, A.g_pan0); UPG(g_pan64_d, A.g_pan64);
+    UPG(g_pan32_d, A.g_pan32); UPG(g_p64_d, A.g_p64); UPG(g_tkb, kb); UPG(g_tib, ib); UPG(g_tr0, r0);
+    UPG(g_tdr, dr);
+    for (int k = 1; k <= 3; ++k) {
+        std::vector<double> r = sauter_schwab(k, A.opts.near_order);
+        A.ss_npp[k] = (int)(r.size() / 5);
+        UPG(ss[k], r);
+    }
+    std::vector<double> dummy(5, 0.0);
+    UPG(ss[0], dummy);
+#undef UPG
+    const size_t njob = kb.size(), nb = A.blocks.size();
+    if ((s = dev_alloc(A.g_samples, njob * NCHEB * 2 * sizeof(double), st))) return s;
+    if ((s = dev_alloc(A.g_coef, njob * NCHEB * 2 * sizeof(double), st))) return s;
+    if ((s = dev_alloc(A.g_coef32, (size_t)A.g_npan * 68 * sizeof(float), st))) return s;
+    if ((s = dev_alloc(A.gpair, (size_t)E * E * sizeof(double2), st))) return s;
+    if ((s = dev_alloc(A.gvmin, (size_t)M * M * sizeof(double), st))) return s;
+    if ((s = dev_alloc(A.gvmax, (size_t)M * M * sizeof(double), st))) return s;
+    if ((s = dev_alloc(A.gpartial, 1024 * sizeof(double), st))) return s;
+    if ((s = dev_alloc(A.status, 16, st))) return s;
+    if ((s = dev_alloc(A.cnt_far, nb * M * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.cnt_near, nb * M * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.rp_far, nb * (M + 1) * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.rp_near, nb * (M + 1) * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.tot_far, nb * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.tot_near, nb * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.off_far_d, nb * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.off_near_d, nb * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.quad_partial, 1024 * sizeof(int64_t), st))) return s;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    A.nnz_far.assign(nb, -1);
+    A.nnz_near.assign(nb, -1);
+    A.g_njob32 = (int)njob32;
+    return TDBEM_OK;
+}
+
 // ---------------------------------------------------------------- C ABI
 extern "C" {
 
@@ -557,7 +767,6 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
                                     void *stream, tdbem_asm **out) {
     if (!out || !mesh || !tg) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (!tg->equidistant) return fail(TDBEM_E_UNSUPPORTED, "this build assembles equidistant time grids only");
     if (tg->N < 5 || tg->N > 1000) return fail(TDBEM_E_UNSUPPORTED, "need 5 <= N <= 1000 grid points");
     if (tg->c != 1.0 && tg->c <= 0.0) return fail(TDBEM_E_INVALID_ARG, "bad wave speed");
     tdbem_opts o{};
@@ -575,6 +784,12 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     A->opts = o;
     A->fp64 = o.precision == TDBEM_PREC_FP64;
     auto bail = [&](tdbem_status s) { delete A; return s; };
+    if (!tg->equidistant) {
+        tdbem_status gs = create_graded(*A, st);
+        if (gs) return bail(gs);
+        *out = A;
+        return TDBEM_OK;
+    }
     tdbem_status s = plan_blocks(*A);
     if (s) return bail(s);
     const double dt = tg->dt;
@@ -757,6 +972,7 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
         d.col_near = (const int32_t *)A.col_near.p + A.off_near[b];
         d.val_near = (const double *)A.val_near.p + A.off_near[b];
         block_run(A.blocks[b].kb, A.blocks[b].ib, N, d.k0, d.i0, d.cnt);
+        if (A.graded) d.cnt = 1;  // graded grid: every block stands only for itself
     }
     tdbem_status s;
     if ((s = upload(A.mv_blk, A.mv_host, st))) return s;
@@ -1046,9 +1262,265 @@ static tdbem_status assemble_replay(tdbem_asm *A, cudaStream_t st) {
     return TDBEM_OK;
 }
 
+static GradedArgs make_gargs(tdbem_asm *A) {
+    const tdbem_mesh &m = *A->mesh;
+    GradedArgs a{};
+    a.g = make_geo(A);
+    a.N = (int)A->tg->N;
+    a.tie = 1e-12 * A->tg->T;
+    a.pair = (const double2 *)A->gpair.p;
+    a.vmin = (const double *)A->gvmin.p;
+    a.vmax = (const double *)A->gvmax.p;
+    a.ga = (const double *)A->g_ga_d.p;
+    a.gb = (const double *)A->g_gb_d.p;
+    a.colblk = (const int *)A->g_colblk_d.p;
+    a.colk0 = (const int *)A->g_colk0_d.p;
+    a.pan0 = (const int *)A->g_pan0_d.p;
+    a.pan64 = (const GPan64 *)A->g_pan64_d.p;
+    a.pan32 = (const float4 *)A->g_pan32_d.p;
+    a.coef32 = (const float *)A->g_coef32.p;
+    a.coef64 = (const double *)A->g_coef.p + (size_t)A->g_njob32 * NCHEB * 2;
+    a.p64 = (const int *)A->g_p64_d.p;
+    a.S64 = A->S64;
+    a.maxpan = A->g_maxpan;
+    a.kw = (const int *)A->g_kw_d.p;
+    a.dense = (double *)A->g_dense.p;
+    a.ndense = (double *)A->g_ndense.p;
+    a.NB = m.NB;
+    a.all_tris = (const int32_t *)A->colors.p;
+    a.col_off = (const int64_t *)A->g_coloff_d.p;
+    a.ncol = (int)A->color_off.size() - 1;
+    a.cenh = (const float *)A->g_cenh.p;
+    a.cenl = (const float *)A->g_cenl.p;
+    a.geoh = (const float *)A->geo32.p;
+    a.geol = (const float *)A->g_geol.p;
+    a.adj_ptr = (const int64_t *)A->adj_ptr.p;
+    a.adj_tri = (const int32_t *)A->adj_tri.p;
+    a.adj_perm = (const int8_t *)A->adj_perm.p;
+    a.adj_nbr = (const int32_t *)A->adj_nbr.p;
+    for (int k = 0; k < 4; ++k) { a.ss_xy[k] = (const double *)A->ss[k].p; a.ss_npp[k] = A->ss_npp[k]; }
+    a.rule_w64 = (const double *)A->rule_w64.p;
+    a.rule_l64 = (const double *)A->rule_l64.p;
+    for (int k = 0; k < 7; ++k) {
+        a.wwh[k] = (float)m.rule_W[k];
+        a.wwl[k] = (float)(m.rule_W[k] - (double)a.wwh[k]);
+        for (int d = 0; d < 3; ++d) {
+            const double gw = m.rule_W[k] * m.rule_L[k][d];
+            a.gwh[3 * k + d] = (float)gw;
+            a.gwl[3 * k + d] = (float)(gw - (double)a.gwh[3 * k + d]);
+        }
+    }
+    a.status = (int *)A->status.p;
+    return a;
+}
+
+// Window lengths per column and the batches of trial columns whose FP64
+// windows fit the staging budget; (re)allocates the staging buffers.
+static tdbem_status plan_graded_batches(tdbem_asm &A, double smax, cudaStream_t st) {
+    const int64_t N = A.tg->N, M = A.mesh->M, NB = A.mesh->NB;
+    A.g_kw.assign(N, 1);
+    for (int64_t i = 0; i < N; ++i) A.g_kw[i] = graded_kw(A, i, smax);
+    size_t fr = 0, tot = 0;
+    CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+    const size_t cap = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, fr / 4));
+    A.g_bi0.clear();
+    A.g_bi1.clear();
+    A.g_doff.assign(N, 0);
+    A.g_ndoff.assign(N, 0);
+    A.g_dense_max = A.g_ndense_max = 0;
+    int64_t i = 0;
+    while (i < N) {
+        size_t d = 0, nd = 0;
+        int64_t j = i;
+        while (j < N) {
+            const size_t fd = (size_t)M * M * A.g_kw[j] * sizeof(double);
+            const size_t fn = (size_t)M * NB * A.g_kw[j] * sizeof(double);
+            if (j > i && d + fd + nd + fn > cap) break;
+            A.g_doff[j] = (int64_t)(d / sizeof(double));
+            A.g_ndoff[j] = (int64_t)(nd / sizeof(double));
+            d += fd;
+            nd += fn;
+            ++j;
+        }
+        A.g_bi0.push_back((int)i);
+        A.g_bi1.push_back((int)j);
+        A.g_dense_max = std::max(A.g_dense_max, d);
+        A.g_ndense_max = std::max(A.g_ndense_max, nd);
+        i = j;
+    }
+    tdbem_status s;
+    if ((s = upload(A.g_kw_d, A.g_kw, st))) return s;
+    if ((s = upload(A.g_doff_d, A.g_doff, st))) return s;
+    if ((s = upload(A.g_ndoff_d, A.g_ndoff, st))) return s;
+    if (A.g_dense.n < A.g_dense_max)
+        if ((s = dev_alloc(A.g_dense, A.g_dense_max, st))) return s;
+    if (A.g_ndense.n < A.g_ndense_max)
+        if ((s = dev_alloc(A.g_ndense, A.g_ndense_max, st))) return s;
+    A.g_smax = smax;
+    return TDBEM_OK;
+}
+
+// One assembly on a graded grid (always eager): psi tables, element- and
+// vertex-pair bounds, row counts and CSR sizes, then per batch of trial
+// columns the far field (one launch per test colour), the near field and the
+// CSR fill of the batch's blocks.
+static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
+    const tdbem_mesh &m = *A->mesh;
+    const int64_t M = m.M, E = m.E;
+    const size_t nb = A->blocks.size();
+    for (auto &e : A->ev)
+        if (!e) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(A->ev[0], st));
+    CUDA_TRY(cudaMemsetAsync(A->status.p, 0, 16, st));
+    // ---- psi tables: FP32 set (24-point Gauss-Legendre x 4 per piece), FP64 sets (x 8), DCT
+    const int nj32 = A->g_njob32, nj64 = A->g_nset64;
+    launch_psi_samples_var((const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p, (const int *)A->g_tib.p,
+                           (const double *)A->g_tr0.p, (const double *)A->g_tdr.p, nj32, (const double *)A->gl_x.p,
+                           (const double *)A->gl_w.p, 24, 4, (double *)A->g_samples.p, st);
+    launch_psi_samples_var((const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p + nj32,
+                           (const int *)A->g_tib.p + nj32, (const double *)A->g_tr0.p + nj32,
+                           (const double *)A->g_tdr.p + nj32, nj64, (const double *)A->gl_x.p,
+                           (const double *)A->gl_w.p, 24, 8, (double *)A->g_samples.p + (size_t)nj32 * NCHEB * 2, st);
+    launch_psi_dct((const double *)A->g_samples.p, nj32 + nj64, (double *)A->g_coef.p, st);
+    if (!A->fp64) launch_gcoef32((const double *)A->g_coef.p, A->g_npan, (float *)A->g_coef32.p, st);
+    CUDA_TRY(cudaGetLastError());
+    // ---- bounds, windows, row counts, CSR sizes
+    Geo g = make_geo(A);
+    launch_gpair_bounds(g, (double2 *)A->gpair.p, st);
+    GradedArgs ga = make_gargs(A);
+    launch_gvertex(ga, (double *)A->gvmin.p, (double *)A->gvmax.p, (double *)A->gpartial.p, 1024, st);
+    launch_gcount(ga, (const int *)A->g_cb2api_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
+                  (int64_t *)A->cnt_far.p, (int64_t *)A->cnt_near.p, st);
+    launch_scan_rows((const int64_t *)A->cnt_far.p, M, (int)nb, (int64_t *)A->rp_far.p, (int64_t *)A->tot_far.p, st);
+    launch_scan_rows((const int64_t *)A->cnt_near.p, M, (int)nb, (int64_t *)A->rp_near.p, (int64_t *)A->tot_near.p, st);
+    launch_gcount_quad(ga, 49, A->ss_npp, (int64_t *)A->quad_partial.p, 1024, st);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(A->ev[1], st));
+    std::vector<double> part(1024);
+    std::vector<int64_t> qp(1024);
+    A->nnz_far.assign(nb, 0);
+    A->nnz_near.assign(nb, 0);
+    CUDA_TRY(cudaMemcpyAsync(part.data(), A->gpartial.p, 1024 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(qp.data(), A->quad_partial.p, 1024 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(A->nnz_far.data(), A->tot_far.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(A->nnz_near.data(), A->tot_near.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    double smax = 0.0;
+    for (double v : part) smax = std::max(smax, v);
+    tdbem_status s;
+    if (smax != A->g_smax)
+        if ((s = plan_graded_batches(*A, smax, st))) return s;
+    A->off_far.assign(nb + 1, 0);
+    A->off_near.assign(nb + 1, 0);
+    for (size_t b = 0; b < nb; ++b) {
+        A->off_far[b + 1] = A->off_far[b] + A->nnz_far[b];
+        A->off_near[b + 1] = A->off_near[b] + A->nnz_near[b];
+    }
+    const size_t rs = A->fp64 ? 8 : 4;
+    if ((size_t)A->off_far[nb] > A->col_far_cap || A->col_far.p == nullptr) {
+        if ((s = dev_alloc(A->col_far, A->off_far[nb] * sizeof(int32_t), st))) return s;
+        if ((s = dev_alloc(A->val_far, A->off_far[nb] * rs, st))) return s;
+        A->col_far_cap = A->off_far[nb];
+    }
+    if ((size_t)A->off_near[nb] > A->col_near_cap || A->col_near.p == nullptr) {
+        if ((s = dev_alloc(A->col_near, A->off_near[nb] * sizeof(int32_t), st))) return s;
+        if ((s = dev_alloc(A->val_near, A->off_near[nb] * sizeof(double), st))) return s;
+        A->col_near_cap = A->off_near[nb];
+    }
+    CUDA_TRY(cudaMemcpyAsync(A->off_far_d.p, A->off_far.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(A->off_near_d.p, A->off_near.data(), nb * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    // ---- per batch of trial columns: far, near, fill
+    ga = make_gargs(A);
+    int dev = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const size_t nbt = A->g_bi0.size();
+    const size_t nev = 3 * nbt + 1;
+    while (A->g_ev.size() < nev) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        A->g_ev.push_back(e);
+    }
+    const size_t smem = gfar_smem(A->g_maxpan, A->fp64);
+    if (smem > 227 * 1024) return fail(TDBEM_E_UNSUPPORTED, "panel tables of one block column exceed shared memory");
+    const int ncol = (int)A->color_off.size() - 1;
+    int64_t launches = 11;
+    for (size_t bt = 0; bt < nbt; ++bt) {
+        const int i0 = A->g_bi0[bt], i1 = A->g_bi1[bt];
+        ga.i0 = i0;
+        ga.i1 = i1;
+        ga.doff = (const int64_t *)A->g_doff_d.p + i0;
+        ga.ndoff = (const int64_t *)A->g_ndoff_d.p + i0;
+        size_t db = 0, ndb = 0;
+        for (int i = i0; i < i1; ++i) {
+            db += (size_t)M * M * A->g_kw[i] * sizeof(double);
+            ndb += (size_t)M * m.NB * A->g_kw[i] * sizeof(double);
+        }
+        CUDA_TRY(cudaMemsetAsync(A->g_dense.p, 0, db, st));
+        CUDA_TRY(cudaMemsetAsync(A->g_ndense.p, 0, ndb, st));
+        CUDA_TRY(cudaEventRecord(A->g_ev[3 * bt], st));
+        for (int c = 0; c < ncol; ++c) {
+            ga.color_tris = (const int32_t *)A->colors.p + A->color_off[c];
+            ga.ncolor = A->color_off[c + 1] - A->color_off[c];
+            if (ga.ncolor <= 0) continue;
+            launch_gfar(ga, A->fp64, (int)std::min<int64_t>(ga.ncolor, nsm), smem, st);
+            ++launches;
+        }
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(A->g_ev[3 * bt + 1], st));
+        for (int c = 0; c < ncol; ++c) {
+            ga.color_tris = (const int32_t *)A->colors.p + A->color_off[c];
+            ga.ncolor = A->color_off[c + 1] - A->color_off[c];
+            if (ga.ncolor <= 0) continue;
+            launch_gnear(ga, (int)std::min<int64_t>(ga.ncolor, 4 * (int64_t)nsm), st);
+            ++launches;
+        }
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(A->g_ev[3 * bt + 2], st));
+        launch_gfill(ga, (const int *)A->g_cb2api_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
+                     (const int64_t *)A->rp_far.p, (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p,
+                     A->val_far.p, A->fp64, (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p,
+                     (int32_t *)A->col_near.p, (double *)A->val_near.p, st);
+        ++launches;
+        CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaEventRecord(A->g_ev[3 * nbt], st));
+    int status = 0;
+    CUDA_TRY(cudaMemcpyAsync(&status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    float ms_pat = 0.f, ms_far = 0.f, ms_near = 0.f, ms_ext = 0.f, x = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms_pat, A->ev[0], A->ev[1]));
+    for (size_t bt = 0; bt < nbt; ++bt) {
+        CUDA_TRY(cudaEventElapsedTime(&x, A->g_ev[3 * bt], A->g_ev[3 * bt + 1])); ms_far += x;
+        CUDA_TRY(cudaEventElapsedTime(&x, A->g_ev[3 * bt + 1], A->g_ev[3 * bt + 2])); ms_near += x;
+        CUDA_TRY(cudaEventElapsedTime(&x, A->g_ev[3 * bt + 2], A->g_ev[3 * bt + 3])); ms_ext += x;
+    }
+    A->stats.n_blocks = (int64_t)nb;
+    A->stats.nnz = A->off_far[nb];
+    A->stats.nnz_near = A->off_near[nb];
+    int64_t q = 0;
+    for (int64_t v : qp) q += v;
+    A->stats.quad_points = q;
+    int64_t nearp = 0;
+    for (int64_t t = 0; t < E; ++t) nearp += m.adj_ptr[t + 1] - m.adj_ptr[t];
+    A->stats.near_pairs = nearp;
+    A->stats.far_pairs = E * E - nearp;
+    A->stats.ms_pattern = ms_pat;
+    A->stats.ms_far = ms_far;
+    A->stats.ms_near = ms_near;
+    A->stats.ms_extract = ms_ext;
+    A->stats.ms_total = ms_pat + ms_far + ms_near + ms_ext;
+    A->stats.kernel_launches = launches;
+    if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
+    if ((s = plan_matvec(*A, st))) return s;
+    A->assembled = true;
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
     cudaStream_t st = (cudaStream_t)stream;
+    if (A->graded) return assemble_graded(A, st);
     if (A->assembled && A->use_graph) return assemble_replay(A, st);
     return assemble_body(A, st, false);
 }

@@ -180,6 +180,29 @@ void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStr
     pair_bounds_kernel<<<grid, 128, 0, st>>>(g, lt, rec);
 }
 
+// Graded grids: exact FP64 bounds (dmin, dmax) of every element pair (dmin
+// = 0 when the triangles share a vertex); the kept blocks follow from them
+// per trial column (Sec. 3.2).
+__global__ void gpair_bounds_kernel(Geo g, double2 *out) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // trial
+    const int64_t q = blockIdx.y;                                       // test
+    if (s >= g.E) return;
+    const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
+    int shared = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) shared += (A[i] == B[j]);
+    d3 ad[3], bd[3];
+    for (int i = 0; i < 3; ++i) { ad[i] = ld3(g.V + 3 * A[i]); bd[i] = ld3(g.V + 3 * B[i]); }
+    double dn2, dx2;
+    tri_bounds2<d3, double>(ad, bd, shared != 0, dn2, dx2);
+    out[q * g.E + s] = make_double2(sqrt(dn2), sqrt(dx2));
+}
+
+void launch_gpair_bounds(const Geo &g, double2 *out, cudaStream_t st) {
+    dim3 grid((unsigned)((g.E + 127) / 128), (unsigned)g.E);
+    gpair_bounds_kernel<<<grid, 128, 0, st>>>(g, out);
+}
+
 // --------------------------------------------------- vertex-pair windows
 // Window of vertex pair (l, j): union over tau in star(l), sigma in star(j)
 // of the element-pair lag ranges (an interval, since both stars are

@@ -107,15 +107,17 @@ __device__ static void psi_direct(const double *t, int N, int kb, int ib, double
 }
 
 // One thread per (sub-panel, Chebyshev node). Sub-panel p covers
-// r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]).
+// r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]); with pdr given, its
+// width is pdr[p] instead (uneven panels of a graded grid).
 __global__ void psi_samples_kernel(const double *t, int N, const int *pkb, const int *pib,
-                                   const double *pr0, double dr, int total, const double *gx,
+                                   const double *pr0, double dr, const double *pdr, int total, const double *gx,
                                    const double *gw, int gn, int gsub, double *samples) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total * NCHEB) return;
     const int p = id / NCHEB, m = id % NCHEB;
     const double xm = cos(M_PI * (m + 0.5) / NCHEB);
-    const double r = pr0[p] + 0.5 * dr * (xm + 1.0);
+    const double w = pdr ? pdr[p] : dr;
+    const double r = pr0[p] + 0.5 * w * (xm + 1.0);
     double a, b;
     psi_direct(t, N, pkb[p], pib[p], r, gx, gw, gn, gsub, a, b);
     samples[2 * id + 0] = a;
@@ -146,8 +148,17 @@ void launch_psi_samples(const double *t, int N, const int *panel_class, const in
     (void)panel_class; (void)S;
     const int n = total_sub * NCHEB;
     psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(t, N, panel_kb, panel_ib, panel_r0,
-                                                       panel_dr, total_sub, gl_x, gl_w, gl_n,
+                                                       panel_dr, nullptr, total_sub, gl_x, gl_w, gl_n,
                                                        gl_sub, samples);
+}
+
+void launch_psi_samples_var(const double *t, int N, const int *panel_kb, const int *panel_ib,
+                            const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
+                            const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st) {
+    const int n = total_sub * NCHEB;
+    if (n <= 0) return;
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(t, N, panel_kb, panel_ib, panel_r0, 0.0, panel_dr,
+                                                       total_sub, gl_x, gl_w, gl_n, gl_sub, samples);
 }
 
 void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st) {

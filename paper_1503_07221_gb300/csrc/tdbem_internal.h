@@ -108,9 +108,15 @@ void launch_psi_samples(const double *t, int N, const int *panel_class, const in
                         int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                         double *samples, cudaStream_t st);
 void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st);
+// sub-panel p covers [r0[p], r0[p] + dr[p]] (uneven panels)
+void launch_psi_samples_var(const double *t, int N, const int *panel_kb, const int *panel_ib,
+                            const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
+                            const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st);
 
 // pattern.cu
 void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st);
+// graded grids: exact (dmin, dmax) of every element pair, E x E
+void launch_gpair_bounds(const Geo &g, double2 *out, cudaStream_t st);
 void launch_vertex_windows(const Geo &g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
                            uint8_t *smask, int KW, int *status, cudaStream_t st);
 void launch_count_quad(const Geo &g, const PairRec *rec, const int *npp, int64_t *partial,
@@ -289,6 +295,85 @@ class KrylovSolver {
                              cudaStream_t st);
     cudaError_t read_head(KHead *h, cudaStream_t st);
 };
+
+// graded.cu: assembly on a non-equidistant time grid, where every nonzero
+// block (k, i) with i <= k + 1 is its own unique block (no reuse along the
+// diagonals). Blocks are numbered column-major internally: column i holds
+// blocks k = colk0[i] .. colk0[i] + (colblk[i+1] - colblk[i]) - 1, a
+// contiguous range (the supports a, b grow with k). Each block has GP_MAXPAN
+// or fewer panels between the breakpoints t_{k-a} - t_{i-b} of psi.
+constexpr int GP_MAXPAN = 8;
+struct alignas(32) GPan64 {  // FP64 panel: start, width, S64 / width, unused
+    double x, y, z, w;
+};     // panels of one block
+constexpr int GP_KSLOT = 4;      // blocks one far warp evaluates at a time
+constexpr int GP_MAXK = 256;     // blocks of one trial column
+constexpr int GF_WARPS = 16;     // warps of a far CTA
+constexpr int GN_WARPS = 8;      // warps of a near CTA
+constexpr int GN_TILE = 512;     // near point pairs staged at a time
+struct GradedArgs {
+    Geo g;
+    int N;
+    double tie;
+    const double2 *pair;      // E x E element-pair (dmin, dmax)
+    const double *vmin;       // M x M vertex-pair Dmin (min over the two stars)
+    const double *vmax;       // M x M vertex-pair Dmax
+    const double *ga, *gb;    // support (a, b) per column-major block
+    const int *colblk;        // N + 1
+    const int *colk0;         // N
+    const int *pan0;          // column-major block -> first panel (nblk + 1)
+    const GPan64 *pan64;     // per panel: (start, width, -, -)
+    const float4 *pan32;      // per panel: (start_h, mid_h, mid_l, 2/width)
+    const float *coef32;      // per panel: 34 x (psi, psi~), FP32 (entry 33 zero)
+    const double *coef64;     // per FP64 coefficient set: 33 x (psi, psi~)
+    const int *p64;           // per panel: first of its S64 FP64 sets (-1: none)
+    int S64;
+    int maxpan;               // most panels of one column
+    // batch of trial columns [i0, i1) and its staging windows
+    int i0, i1;
+    const int64_t *doff;      // per batch column: offset (doubles) of its far windows
+    const int64_t *ndoff;     // per batch column: offset of its near windows
+    const int *kw;            // per column: window length KW_i
+    double *dense;            // far: [l][j][KW_i] per batch column
+    double *ndense;           // near: [l][nbr index][KW_i] per batch column
+    int NB;
+    // triangles
+    const int32_t *color_tris; // test triangles of this launch (one colour)
+    int64_t ncolor;
+    const int32_t *all_tris;  // every triangle, grouped by colour
+    const int64_t *col_off;   // colour offsets into all_tris (ncol + 1)
+    int ncol;
+    const float *cenh, *cenl; // E x 3 centroids as FP32 pairs
+    const float *geoh, *geol; // E x 16 geometry (n, area, curls) as FP32 pairs
+    // near field
+    const int64_t *adj_ptr;
+    const int32_t *adj_tri;
+    const int8_t *adj_perm;
+    const int32_t *adj_nbr;
+    const double *ss_xy[4];
+    int ss_npp[4];
+    // 7-point rule: weights, barycentrics, w_k lambda_a(p_k) and w_k as FP32 pairs
+    const double *rule_w64, *rule_l64;
+    float gwh[21], gwl[21], wwh[7], wwl[7];
+    int *status;
+};
+void launch_gfar(const GradedArgs &a, bool fp64, int grid, size_t smem, cudaStream_t st);
+void launch_gnear(const GradedArgs &a, int grid, cudaStream_t st);
+// per (row, column): far and near row counts of every block of the column
+void launch_gcount(const GradedArgs &a, const int *cb2api, const int64_t *nbr_ptr, const int32_t *nbr,
+                   int64_t *cnt_far, int64_t *cnt_near, cudaStream_t st);
+// vertex-pair Dmin / Dmax and per-CTA maxima of Dmax - Dmin (partial, nblocks entries)
+void launch_gvertex(const GradedArgs &a, double *vmin, double *vmax, double *partial, int nblocks, cudaStream_t st);
+// quadrature point pairs x kept blocks over all element pairs (per-CTA partial sums)
+void launch_gcount_quad(const GradedArgs &a, int npp_far, const int *npp_near, int64_t *partial, int nblocks,
+                        cudaStream_t st);
+// CSR fill of the blocks of batch columns [a.i0, a.i1)
+void launch_gfill(const GradedArgs &a, const int *cb2api, const int64_t *nbr_ptr, const int32_t *nbr,
+                  const int64_t *rp_far, const int64_t *off_far, int32_t *col_far, void *val_far, bool fp64,
+                  const int64_t *rp_near, const int64_t *off_near, int32_t *col_near, double *val_near,
+                  cudaStream_t st);
+size_t gfar_smem(int max_col_panels, bool fp64);
+void launch_gcoef32(const double *coef, int npan, float *out, cudaStream_t st);
 
 // peaks.cu: FMA throughput of the device (roofline denominators)
 cudaError_t measure_fma_peaks(double *fp32, double *fp64, cudaStream_t st);
