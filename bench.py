@@ -37,12 +37,19 @@ CONFIGS = {
     "sphere20480": "icosphere 20480 triangles / 10242 vertices, N=129 points, dt=0.05 on [0,6.4], c=1, p=0",
     "sphere5120j": "icosphere 5120 / 2562 jittered +-1% h (seed 0), N=65 points, dt=0.0625 on [0,4], c=1, p=0",
     "sphere320": "icosphere 320 / 162, N=17 points, dt=0.25 on [0,4], c=1, p=0",
+    "torus8192g": "torus R=1 r=0.4, 128x32 quads (8192 triangles / 4096 vertices), graded grid of 96 steps "
+                  "with ratio 1.02 on [0,6] (N=97 points), c=1, p=0; every nonzero block assembled",
+    "torus2048g": "torus R=1 r=0.4, 64x16 quads (2048 triangles / 1024 vertices), the same graded grid",
 }
 
 
 def workload(name):
     w = inputs.workload(name)
     return w.verts, w.tris, w.t
+
+
+def is_graded(name):
+    return not inputs.workload(name).equidistant
 
 
 class ClockSampler:
@@ -101,18 +108,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_sample(V, F, t, rows_n, seed=0):
-    """Time the FP64 oracle on a fixed row sample (all unique blocks)."""
+def cpu_sample(V, F, t, rows_n, seed=0, equidistant=True, blocks_n=None):
+    """Time the FP64 oracle on a fixed row sample (all unique blocks, or a
+    seeded sample of blocks_n of them)."""
     from oracle.oracle import Oracle, num_threads
     rng = np.random.default_rng(seed)
     rows = np.sort(rng.choice(V.shape[0], size=rows_n, replace=False))
     t0 = time.perf_counter()
-    o = Oracle(V, F, t, psi_mode="interp")
+    o = Oracle(V, F, t, equidistant=equidistant, psi_mode="interp")
     t1 = time.perf_counter()
-    res = o.assemble_rows(rows, np.arange(o.num_blocks()))
+    nb = o.num_blocks()
+    blks = np.arange(nb) if blocks_n is None else np.sort(rng.choice(nb, size=min(blocks_n, nb), replace=False))
+    res = o.assemble_rows(rows, blks)
     t2 = time.perf_counter()
     nnz = sum(len(c) for b in res.values() for (c, f, n) in b)
-    return {"nnz": nnz, "seconds": t2 - t0, "setup_s": t1 - t0, "rows": int(rows_n), "cores": num_threads()}
+    return {"nnz": nnz, "seconds": t2 - t0, "setup_s": t1 - t0, "rows": int(rows_n), "cores": num_threads(),
+            "blocks": int(blks.size)}
+
+
+def cpu_sample_args(args):
+    # graded grids: every nonzero block is unique (thousands); the oracle then
+    # takes 2 rows x a seeded sample of 60 blocks to stay within ~30 s
+    if is_graded(args.config):
+        return {"rows_n": min(args.cpu_rows, 2), "equidistant": False, "blocks_n": 60}
+    return {"rows_n": args.cpu_rows, "equidistant": True, "blocks_n": None}
 
 
 def run_reference(args):
@@ -120,12 +139,11 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    rows_n = args.cpu_rows
-    for _ in range(args.warmup if args.warmup < 1 else 0):
-        pass
+    ca = cpu_sample_args(args)
+    rows_n = ca["rows_n"]
     rates, secs = [], []
     for _ in range(args.steps):
-        s = cpu_sample(V, F, t, rows_n)
+        s = cpu_sample(V, F, t, **ca)
         rates.append(s["nnz"] / s["seconds"])
         secs.append(s["seconds"])
     v = float(np.median(rates))
@@ -135,9 +153,9 @@ def run_reference(args):
         "ms_per_step": float(np.median(secs)) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.config, "desc": CONFIGS[args.config], "precision": "fp64 oracle",
-                   "sample": "%d random rows (seed 0), all unique blocks" % rows_n},
+                   "sample": "%d random rows (seed 0) x %d unique blocks" % (rows_n, s["blocks"])},
         "cpu_baseline": {"value": v, "unit": "nonzeros/s", "cores": s["cores"], "kind": "oracle",
-                         "sample": "%d rows x all unique blocks of %s" % (rows_n, args.config)},
+                         "sample": "%d rows x %d unique blocks of %s" % (rows_n, s["blocks"], args.config)},
         "e2e": {"value": v, "unit": "nonzeros/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -151,6 +169,15 @@ def far_flops(st):
     # equivalents), weights (4 FMA), accumulation 10 panels x 4 (40 FMA):
     # 621 FMA = 1242 FLOP. Compensation terms are not counted.
     return 1242.0 * st["far_pairs"] * 49
+
+
+def gfar_flops(st):
+    # graded grids (gfar_kernel): per far point pair and kept block, the T_n
+    # recurrence (31 FMA) and the sums over 33 coefficients of psi and psi~
+    # (66 FMA): 194 FLOP; 1/r scaling (2) and the four weighted sums (8):
+    # 204 FLOP; per far point pair the distance and its FP64-anchored
+    # correction, ~28 FLOP. Compensation terms are not counted.
+    return 204.0 * st["quad_points_far"] + 28.0 * st["far_pairs"] * 49
 
 
 def run_ours(args):
@@ -168,9 +195,10 @@ def run_ours(args):
         dist.init_process_group("nccl")
     tdbem.use_torch_allocator()
     V, F, t = workload(args.config)
+    graded = is_graded(args.config)
     prec = tdbem.PREC_MIXED if args.precision == "mixed" else tdbem.PREC_FP64
     mesh, grid = tdbem.Mesh(V, F), tdbem.TimeGrid(t)
-    asm = tdbem.Assembler(mesh, grid, precision=prec)
+    asm = tdbem.Assembler(mesh, grid, precision=prec, staging_mb=args.staging_mb)
     stream = torch.cuda.current_stream()
     N, M = t.size, V.shape[0]
     # matvec inputs: x_r ~ N(0, 1) from a CPU generator with seed r, copied once
@@ -226,10 +254,16 @@ def run_ours(args):
         bi = asm.block_info(b)
         k, i = bi["k"], bi["i"]
         reuse = (N - 1 - k) if (i == 1 and 1 <= k <= N - 2) else ((N - 3) if (k == 1 and i == 2) else 1)
+        if graded:
+            reuse = 1
         mv_work += (bi["nnz_far"] + bi["nnz_near"]) * reuse
     # end to end through the C ABI: host mesh, grid and right-hand sides in,
     # assembly, matvecs, every result back to host
     e2e = None
+    if graded and args.e2e:
+        # the graded workload holds ~80 GB of CSR: free it before the second assembler
+        del asm
+        torch.cuda.empty_cache()
     if args.e2e:
         Xh = X.cpu().pin_memory()
         Yh = torch.empty((max(args.matvecs, 1), N, M), dtype=torch.float64).pin_memory()
@@ -251,7 +285,7 @@ def run_ours(args):
                "d2h_bytes_per_step": int(Yh[:args.matvecs].numel() * 8)}
     # roofline of the dominant kernel (far field): FP32 FMA pipe
     far_avg_ms = float(np.mean(far_ms))
-    flops = far_flops(st)
+    flops = gfar_flops(st) if graded else far_flops(st)
     achieved = flops / (far_avg_ms * 1e-3) / 1e12
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     peak_nominal = sm_count * 128 * 2 * 2.070e9 / 1e12
@@ -260,7 +294,7 @@ def run_ours(args):
     peak = peak32
     clocks = clk.summary()
     fp64_cmp = None
-    if args.fp64_compare and prec == tdbem.PREC_MIXED:
+    if args.fp64_compare and prec == tdbem.PREC_MIXED and not graded:
         y_mixed = asm.hessenberg_apply(X[0]).cpu()
         del asm
         torch.cuda.empty_cache()
@@ -288,10 +322,10 @@ def run_ours(args):
         del a64
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        s = cpu_sample(V, F, t, args.cpu_rows)
+        s = cpu_sample(V, F, t, **cpu_sample_args(args))
         cpu = {"value": s["nnz"] / s["seconds"], "unit": "nonzeros/s", "cores": s["cores"], "kind": "oracle",
-               "sample": "%d random rows (seed 0) x all %d unique blocks, %.1f s incl. %.1f s psi interpolant setup"
-                         % (s["rows"], nb, s["seconds"], s["setup_s"])}
+               "sample": "%d random rows (seed 0) x %d of %d unique blocks, %.1f s incl. %.1f s psi interpolant "
+                         "setup" % (s["rows"], s["blocks"], nb, s["seconds"], s["setup_s"])}
     if rank == 0:
         line = {
             "metric": "assembled nonzeros/s", "value": value, "unit": "nonzeros/s", "n_gpus": world,
@@ -309,7 +343,7 @@ def run_ours(args):
             "matvec_nnz_reuse_per_s": mv_work * world / (mv_ms * 1e-3) if args.matvecs else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "far32_kernel (FP32 FMA pipe)",
+                         "kernel": ("gfar_kernel<false>" if graded else "far32_kernel") + " (FP32 FMA pipe)",
                          "peak_basis": "measured: packed FP32 FMA microbenchmark (tdbem_measure_fma_peaks) "
                                        "after the timed region",
                          "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
@@ -334,6 +368,8 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=16)
     ap.add_argument("--matvecs", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--staging-mb", type=int, default=0,
+                    help="non-equidistant grids: cap on the staging windows of one batch (MiB, 0 = default)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     args = ap.parse_args()

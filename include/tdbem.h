@@ -103,7 +103,9 @@ typedef struct {
     int32_t precision;     /* TDBEM_PREC_FP64 or TDBEM_PREC_MIXED */
     int32_t near_order;    /* Gauss-Legendre points per direction, Sauter-Schwab (default 4) */
     int32_t cheb_degree;   /* Chebyshev degree per panel (32; the only value this build takes) */
-    int32_t reserved[5];
+    int32_t staging_mb;    /* non-equidistant grids: cap (MiB) on the FP64 staging windows of one
+                              batch of block columns; 0 = a quarter of the free memory, <= 24 GiB */
+    int32_t reserved[4];
 } tdbem_opts;
 
 typedef struct {
@@ -121,6 +123,7 @@ typedef struct {
     int64_t kernel_launches; /* kernels launched by the last tdbem_assemble_all */
     int64_t graph_replays;   /* assemblies replayed from the recorded CUDA graph */
     int64_t matvec_variant;  /* matvec launch shape chosen by the autotuner (-1: not tuned yet) */
+    int64_t quad_points_far; /* of quad_points: far element pairs (non-equidistant grids; -1 otherwise) */
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */

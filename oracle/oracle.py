@@ -227,6 +227,14 @@ class Oracle:
         lib().or_pair_local(self.h, s, q, blks, blks.size, far_n, near_n, L)
         return L.reshape(blks.size, 3, 3)
 
+    def pattern_counts(self, rows, blks):
+        """Structural entries of rows `rows` in blocks `blks`: (nb, nr) int64."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        blks = np.ascontiguousarray(blks, dtype=np.int64)
+        counts = np.zeros(rows.size * blks.size, np.int64)
+        lib().or_pattern_counts(self.h, rows, rows.size, blks, blks.size, counts)
+        return counts.reshape(blks.size, rows.size)
+
     def assemble_rows(self, rows, blks):
         """Rows `rows` of blocks `blks`: dict blk -> list over rows of
         (cols int32, far float64, near float64)."""

@@ -671,7 +671,7 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
     const size_t njob = kb.size(), nb = A.blocks.size();
     if ((s = dev_alloc(A.g_samples, njob * NCHEB * 2 * sizeof(double), st))) return s;
     if ((s = dev_alloc(A.g_coef, njob * NCHEB * 2 * sizeof(double), st))) return s;
-    if ((s = dev_alloc(A.g_coef32, (size_t)A.g_npan * 68 * sizeof(float), st))) return s;
+    if ((s = dev_alloc(A.g_coef32, (size_t)A.g_npan * 76 * sizeof(float), st))) return s;
     if ((s = dev_alloc(A.gpair, (size_t)E * E * sizeof(double2), st))) return s;
     if ((s = dev_alloc(A.gvmin, (size_t)M * M * sizeof(double), st))) return s;
     if ((s = dev_alloc(A.gvmax, (size_t)M * M * sizeof(double), st))) return s;
@@ -685,7 +685,7 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
     if ((s = dev_alloc(A.tot_near, nb * sizeof(int64_t), st))) return s;
     if ((s = dev_alloc(A.off_far_d, nb * sizeof(int64_t), st))) return s;
     if ((s = dev_alloc(A.off_near_d, nb * sizeof(int64_t), st))) return s;
-    if ((s = dev_alloc(A.quad_partial, 1024 * sizeof(int64_t), st))) return s;
+    if ((s = dev_alloc(A.quad_partial, 2048 * sizeof(int64_t), st))) return s;
     CUDA_TRY(cudaStreamSynchronize(st));
     A.nnz_far.assign(nb, -1);
     A.nnz_near.assign(nb, -1);
@@ -777,6 +777,7 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     if (o.precision != TDBEM_PREC_FP64 && o.precision != TDBEM_PREC_MIXED) return fail(TDBEM_E_INVALID_ARG, "precision");
     if (o.near_order < 1 || o.near_order > 5) return fail(TDBEM_E_INVALID_ARG, "near_order must be in 1..5");
     if (o.cheb_degree != 32) return fail(TDBEM_E_UNSUPPORTED, "cheb_degree must be 32");
+    if (o.staging_mb < 0) return fail(TDBEM_E_INVALID_ARG, "staging_mb must be >= 0");
     cudaStream_t st = (cudaStream_t)stream;
     tdbem_asm *A = new tdbem_asm();
     A->mesh = mesh;
@@ -1196,6 +1197,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     int64_t q = 0;
     for (int64_t v : qp) q += v;
     A->stats.quad_points = q;
+    A->stats.quad_points_far = -1;
     int64_t nearp = 0;
     for (int64_t t = 0; t < E; ++t) nearp += m.adj_ptr[t + 1] - m.adj_ptr[t];
     A->stats.near_pairs = nearp;
@@ -1322,7 +1324,8 @@ static tdbem_status plan_graded_batches(tdbem_asm &A, double smax, cudaStream_t 
     for (int64_t i = 0; i < N; ++i) A.g_kw[i] = graded_kw(A, i, smax);
     size_t fr = 0, tot = 0;
     CUDA_TRY(cudaMemGetInfo(&fr, &tot));
-    const size_t cap = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, fr / 4));
+    size_t cap = std::max<size_t>((size_t)256 << 20, std::min<size_t>((size_t)24 << 30, fr / 4));
+    if (A.opts.staging_mb > 0) cap = (size_t)A.opts.staging_mb << 20;
     A.g_bi0.clear();
     A.g_bi1.clear();
     A.g_doff.assign(N, 0);
@@ -1397,11 +1400,11 @@ static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaEventRecord(A->ev[1], st));
     std::vector<double> part(1024);
-    std::vector<int64_t> qp(1024);
+    std::vector<int64_t> qp(2048);
     A->nnz_far.assign(nb, 0);
     A->nnz_near.assign(nb, 0);
     CUDA_TRY(cudaMemcpyAsync(part.data(), A->gpartial.p, 1024 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(qp.data(), A->quad_partial.p, 1024 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(qp.data(), A->quad_partial.p, 2048 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(A->nnz_far.data(), A->tot_far.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(A->nnz_near.data(), A->tot_near.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1498,9 +1501,10 @@ static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
     A->stats.n_blocks = (int64_t)nb;
     A->stats.nnz = A->off_far[nb];
     A->stats.nnz_near = A->off_near[nb];
-    int64_t q = 0;
-    for (int64_t v : qp) q += v;
+    int64_t q = 0, qf = 0;
+    for (int k = 0; k < 1024; ++k) { q += qp[k]; qf += qp[1024 + k]; }
     A->stats.quad_points = q;
+    A->stats.quad_points_far = qf;
     int64_t nearp = 0;
     for (int64_t t = 0; t < E; ++t) nearp += m.adj_ptr[t + 1] - m.adj_ptr[t];
     A->stats.near_pairs = nearp;

@@ -78,7 +78,11 @@ __device__ __forceinline__ void g_ff_mul(float ah, float al, float b, float &h, 
 // -------------------------------------------------- psi tables of a panel
 // FP32 (mixed far field): Clenshaw recurrence on (psi, psi~) packed, the
 // coefficients as float4 (c_psi[n], c_psi~[n], c_psi[n+1], c_psi~[n+1]),
-// n = 0, 2, .., 32 (entry 33 is zero).
+// n = 0, 2, .., 32 (entry 33 is zero), then the FP32 residuals of c_0..c_3
+// (float4 17 and 18) times T_0..T_3: the rounding of the leading
+// coefficients would otherwise shift psi by the same amount at every point
+// of the panel, an error the quadrature does not average away.
+constexpr int GC32 = 19;  // float4 per panel
 __device__ __forceinline__ void g_cheb32(const float4 *cf, float x, float &ps, float &pt) {
     const gf2 x2 = gpk(2.f * x, 2.f * x);
     gf2 b1 = 0ull, b2 = 0ull;
@@ -97,7 +101,16 @@ __device__ __forceinline__ void g_cheb32(const float4 *cf, float x, float &ps, f
         } else {
             const gf2 xx = gpk(x, x);
             b0 = gfma2(xx, b1, gsub2(gpk(c.x, c.y), b2));   // f = c_0 + x b_1 - b_2
-            gupk(b0, ps, pt);
+            const float4 l01 = cf[17], l23 = cf[18];
+            const float t2 = fmaf(2.f * x, x, -1.f), t3 = fmaf(2.f * x, t2, -x);
+            gf2 cr = gfma2(gpk(t3, t3), gpk(l23.z, l23.w), gpk(l01.x, l01.y));
+            cr = gfma2(gpk(t2, t2), gpk(l23.x, l23.y), cr);
+            cr = gfma2(xx, gpk(l01.z, l01.w), cr);
+            float c0, c1, f0, f1;
+            gupk(cr, c0, c1);
+            gupk(b0, f0, f1);
+            ps = f0 + c0;
+            pt = f1 + c1;
         }
     }
 }
@@ -133,6 +146,142 @@ __device__ __forceinline__ void g_cheb64(const GradedArgs &A, int pg, int np, do
     ps = s0; pt = s1;
 }
 
+// FP32 evaluation of NC panels at once (independent chains, interleaved so
+// the dependent FMA sequences of one lane overlap). T_n by the three-term
+// recurrence; the terms n >= 8 (a few 1e-3 of the panel maximum at most) are
+// summed as the recurrence runs, then the FP32 residuals of c_0..c_3 and the
+// terms n = 7..3 are added, and the three largest terms n = 2, 1, 0 last
+// with exact products and a compensated (two-sum) accumulation. Relative to
+// a plain FP32 Clenshaw sum this lowers the evaluation error about six-fold
+// (CPU emulation at the torus grid: 1e-7 -> 1.5e-8 of the panel maximum).
+template <int NC>
+__device__ __forceinline__ void g_eval32(const float4 *const (&cf)[NC], const float (&x)[NC], float (&ps)[NC],
+                                         float (&pt)[NC]) {
+    float T[NC][8], tm[NC], tc[NC];
+    gf2 hi[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        T[c][0] = 1.f;
+        T[c][1] = x[c];
+#pragma unroll
+        for (int n = 2; n < 8; ++n) T[c][n] = fmaf(2.f * x[c], T[c][n - 1], -T[c][n - 2]);
+        tm[c] = T[c][6];
+        tc[c] = T[c][7];
+        hi[c] = 0ull;
+    }
+#pragma unroll
+    for (int h = 4; h <= 16; ++h) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float4 q = cf[c][h];
+            float t = fmaf(2.f * x[c], tc[c], -tm[c]);
+            tm[c] = tc[c]; tc[c] = t;
+            hi[c] = gfma2(gpk(t, t), gpk(q.x, q.y), hi[c]);  // n = 2h
+            if (2 * h + 1 <= 32) {
+                t = fmaf(2.f * x[c], tc[c], -tm[c]);
+                tm[c] = tc[c]; tc[c] = t;
+                hi[c] = gfma2(gpk(t, t), gpk(q.z, q.w), hi[c]);  // n = 2h + 1
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float4 l01 = cf[c][17], l23 = cf[c][18];
+        gf2 a = hi[c];
+        a = gfma2(gpk(T[c][3], T[c][3]), gpk(l23.z, l23.w), a);
+        a = gfma2(gpk(T[c][2], T[c][2]), gpk(l23.x, l23.y), a);
+        a = gfma2(gpk(T[c][1], T[c][1]), gpk(l01.z, l01.w), a);
+        a = gfma2(gpk(1.f, 1.f), gpk(l01.x, l01.y), a);
+        const float4 q3 = cf[c][3], q2 = cf[c][2], q1 = cf[c][1], q0 = cf[c][0];
+        a = gfma2(gpk(T[c][7], T[c][7]), gpk(q3.z, q3.w), a);
+        a = gfma2(gpk(T[c][6], T[c][6]), gpk(q3.x, q3.y), a);
+        a = gfma2(gpk(T[c][5], T[c][5]), gpk(q2.z, q2.w), a);
+        a = gfma2(gpk(T[c][4], T[c][4]), gpk(q2.x, q2.y), a);
+        a = gfma2(gpk(T[c][3], T[c][3]), gpk(q1.z, q1.w), a);
+        float s0, s1;
+        gupk(a, s0, s1);
+        float k0 = 0.f, k1 = 0.f;
+        const float cc0[3] = {q1.x, q0.z, q0.x}, cc1[3] = {q1.y, q0.w, q0.y};
+        const float tt[3] = {T[c][2], T[c][1], 1.f};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            float p = __fmul_rn(cc0[m], tt[m]), pe = __fmaf_rn(cc0[m], tt[m], -p), sn, e;
+            g_two_sum(s0, p, sn, e);
+            s0 = sn;
+            k0 = __fadd_rn(k0, __fadd_rn(e, pe));
+            p = __fmul_rn(cc1[m], tt[m]);
+            pe = __fmaf_rn(cc1[m], tt[m], -p);
+            g_two_sum(s1, p, sn, e);
+            s1 = sn;
+            k1 = __fadd_rn(k1, __fadd_rn(e, pe));
+        }
+        ps[c] = __fadd_rn(s0, k0);
+        pt[c] = __fadd_rn(s1, k1);
+    }
+}
+
+// Trial points y0 .. y0 + NC - 1 of one lane's (test point, block): distance
+// from the FP64-anchored element-pair geometry, panel, argument, psi and psi~
+// (g_eval32), and the weighted sums t_b += w_y lambda_b(y) psi / r, s~ +=
+// w_y psi~ / r (weights as FP32 pairs). Points outside the block's support
+// contribute zero.
+// (h, l) += (gh + gl) v: exact product error and a two-sum into h
+__device__ __forceinline__ void g_ff_acc(float &h, float &l, float gh, float gl, float v) {
+    const float p = __fmul_rn(gh, v);
+    const float pe = __fmaf_rn(gl, v, __fmaf_rn(gh, v, -p));
+    float s, e;
+    g_two_sum(h, p, s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, pe));
+}
+
+template <int NC>
+__device__ __forceinline__ void g_far_group(const GradedArgs &A, const float4 *scoef, const float4 *smeta, int64_t sg,
+                                            int y0, const float (&ex)[3], const float (&Dn)[3], const float (&Dnl)[3],
+                                            float R0h, float R0l, float fa, float fb, int pb, int pe,
+                                            float (&acc)[8]) {
+    float x[NC], ir[NC], ps[NC], pt[NC];
+    bool in[NC];
+    const float4 *cf[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float *qy = A.g.dq32 + (sg * 7 + y0 + c) * 3;
+        // e = x - y offsets, exactly as a float pair; u = D^.e with D^ a float pair
+        float e0, e1, e2, l0, l1, l2;
+        g_two_sum(ex[0], -qy[0], e0, l0);
+        g_two_sum(ex[1], -qy[1], e1, l1);
+        g_two_sum(ex[2], -qy[2], e2, l2);
+        const float u = fmaf(Dn[0], e0, fmaf(Dn[1], e1, Dn[2] * e2));
+        const float ul = fmaf(Dn[0], l0, fmaf(Dn[1], l1, fmaf(Dn[2], l2, fmaf(Dnl[0], e0, fmaf(Dnl[1], e1, Dnl[2] * e2)))));
+        // r - R0 = u + |e_perp|^2 / ((R0 + u) + r)
+        const float ee = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        const float ep = fmaxf(fmaf(-u, u, ee), 0.f);
+        const float r1 = sqrtf(fmaf(R0h, R0h, fmaf(2.f * R0h, u, ee)));
+        const float q2 = ep / ((R0h + u) + r1);
+        const float sl = R0l + ul + q2;  // small terms of r - R0h
+        const float s = u + sl;
+        const float rr = R0h + s;
+        in[c] = rr > fa && rr < fb;
+        int p = pb;
+        if (in[c])
+            while (p + 1 < pe && rr >= smeta[p + 1].x) ++p;
+        const float4 mt = smeta[p];  // (start, mid_h, mid_l, 2 / width)
+        x[c] = in[c] ? fminf(fmaxf(((R0h - mt.y) + u + (sl - mt.z)) * mt.w, -1.f), 1.f) : 0.f;
+        ir[c] = __frcp_rn(rr);
+        cf[c] = scoef + (size_t)p * GC32;
+    }
+    g_eval32<NC>(cf, x, ps, pt);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int y = y0 + c;
+        const float v = in[c] ? ps[c] * ir[c] : 0.f, vt = in[c] ? pt[c] * ir[c] : 0.f;
+        g_ff_acc(acc[0], acc[1], A.gwh[3 * y], A.gwl[3 * y], v);
+        g_ff_acc(acc[2], acc[3], A.gwh[3 * y + 1], A.gwl[3 * y + 1], v);
+        g_ff_acc(acc[4], acc[5], A.gwh[3 * y + 2], A.gwl[3 * y + 2], v);
+        g_ff_acc(acc[6], acc[7], A.wwh[y], A.wwl[y], vt);
+    }
+}
+
 // ---------------------------------------------------------------- far field
 // CTA = GF_WARPS warps over the test triangles of one colour; per trial
 // column of the batch the column's panel tables are staged in shared memory
@@ -142,9 +291,11 @@ __device__ __forceinline__ void g_cheb64(const GradedArgs &A, int pg, int np, do
 // over the test points are shuffle reductions inside the 8-lane groups.
 size_t gfar_smem(int maxpan, bool fp64) {
     size_t s = 2 * GP_MAXK * sizeof(double) + (GP_MAXK + 4) * sizeof(int);
-    if (!fp64) s += (size_t)maxpan * sizeof(float4) * 18;
+    if (!fp64) s += (size_t)maxpan * sizeof(float4) * (1 + GC32);
     return s;
 }
+
+constexpr int GF_LIST = 1024;  // trial triangles compacted per pass
 
 template <bool FP64>
 __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs A) {
@@ -154,6 +305,8 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
     int *sp0 = reinterpret_cast<int *>(sb + GP_MAXK);
     float4 *smeta = reinterpret_cast<float4 *>(sp0 + GP_MAXK + 4);
     float4 *scoef = smeta + A.maxpan;
+    __shared__ int2 s_list[GF_LIST];  // kept far pairs: (sigma, K1 << 16 | K2)
+    __shared__ int s_cnt, s_next;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xs = lane & 7, ks = lane >> 3;
     const Geo &g = A.g;
@@ -171,8 +324,8 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
         if (threadIdx.x == 0) sp0[nk] = npan;
         if constexpr (!FP64) {
             for (int t = threadIdx.x; t < npan; t += blockDim.x) smeta[t] = A.pan32[pbase + t];
-            const float4 *src = reinterpret_cast<const float4 *>(A.coef32) + (size_t)pbase * 17;
-            for (int t = threadIdx.x; t < npan * 17; t += blockDim.x) scoef[t] = src[t];
+            const float4 *src = reinterpret_cast<const float4 *>(A.coef32) + (size_t)pbase * GC32;
+            for (int t = threadIdx.x; t < npan * GC32; t += blockDim.x) scoef[t] = src[t];
         }
         __syncthreads();
         const int KW = A.kw[ci];
@@ -189,16 +342,48 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                     else ex[d] = g.dq32[(tau * 7 + xs) * 3 + d];
                 }
             for (int c2 = 0; c2 < A.ncol; ++c2) {
-                for (int64_t si = A.col_off[c2] + w; si < A.col_off[c2 + 1]; si += GF_WARPS) {
-                    const int64_t sg = A.all_tris[si];
+                // the colour's trial triangles GF_LIST at a time: (1) each lane decides
+                // one (far pair, kept range) and the kept pairs are compacted into a
+                // shared list; (2) warps take list entries one at a time from a shared
+                // counter (balanced; entries of one trial colour share no vertex, so
+                // the order does not change any sum)
+                const int64_t cend = A.col_off[c2 + 1];
+                for (int64_t pbeg = A.col_off[c2]; pbeg < cend; pbeg += GF_LIST) {
+                  const int64_t pend = min(cend, pbeg + (int64_t)GF_LIST);
+                  if (threadIdx.x == 0) { s_cnt = 0; s_next = 0; }
+                  __syncthreads();
+                  for (int64_t sb0 = pbeg + 32 * w; sb0 < pend; sb0 += 32 * GF_WARPS) {
+                      int K1l = 1, K2l = 0;
+                      int sgl = 0;
+                      if (sb0 + lane < pend) {
+                          sgl = A.all_tris[sb0 + lane];
+                          const int q0 = g.F[3 * (int64_t)sgl], q1 = g.F[3 * (int64_t)sgl + 1], q2 = g.F[3 * (int64_t)sgl + 2];
+                          const bool adj = Ft0 == q0 || Ft0 == q1 || Ft0 == q2 || Ft1 == q0 || Ft1 == q1 ||
+                                           Ft1 == q2 || Ft2 == q0 || Ft2 == q1 || Ft2 == q2;
+                          if (!adj) {
+                              const double2 bd = A.pair[tau * E + sgl];
+                              K1l = g_kfirst(sb, k0, nk, bd.x + A.tie);
+                              K2l = g_klast(sa, k0, nk, bd.y - A.tie);
+                          }
+                      }
+                      const bool keep = K1l <= K2l;
+                      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                      int base = 0;
+                      if (lane == 0 && bal) base = atomicAdd(&s_cnt, __popc(bal));
+                      base = __shfl_sync(0xffffffffu, base, 0);
+                      if (keep) s_list[base + __popc(bal & ((1u << lane) - 1u))] = make_int2(sgl, (K1l << 16) | K2l);
+                  }
+                  __syncthreads();
+                  const int nlist = s_cnt;
+                  for (;;) {
+                    int it = 0;
+                    if (lane == 0) it = atomicAdd(&s_next, 1);
+                    it = __shfl_sync(0xffffffffu, it, 0);
+                    if (it >= nlist) break;
+                    const int2 ent = s_list[it];
+                    const int64_t sg = ent.x;
+                    const int K1 = ent.y >> 16, K2 = ent.y & 0xffff;
                     const int Fs0 = g.F[3 * sg], Fs1 = g.F[3 * sg + 1], Fs2 = g.F[3 * sg + 2];
-                    const bool adj = Ft0 == Fs0 || Ft0 == Fs1 || Ft0 == Fs2 || Ft1 == Fs0 || Ft1 == Fs1 ||
-                                     Ft1 == Fs2 || Ft2 == Fs0 || Ft2 == Fs1 || Ft2 == Fs2;
-                    if (adj) continue;
-                    const double2 bd = A.pair[tau * E + sg];
-                    const int K1 = g_kfirst(sb, k0, nk, bd.x + A.tie);
-                    const int K2 = g_klast(sa, k0, nk, bd.y - A.tie);
-                    if (K1 > K2) continue;
                     // window starts of the nine vertex pairs (lane e = 3a + b)
                     int K1e = 0;
                     if (lane < 9) {
@@ -208,7 +393,7 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                         K1e = g_kfirst(sb, k0, nk, A.vmin[l * M + j] + A.tie);
                     }
                     // element-pair geometry
-                    float R0h = 0.f, R0l = 0.f, Dn[3] = {0.f, 0.f, 0.f};
+                    float R0h = 0.f, R0l = 0.f, Dn[3] = {0.f, 0.f, 0.f}, Dnl[3] = {0.f, 0.f, 0.f};
                     double cd[3] = {0.0, 0.0, 0.0};
                     if constexpr (FP64) {
                         for (int d = 0; d < 3; ++d) cd[d] = g.cen[3 * tau + d] - g.cen[3 * sg + d];
@@ -234,7 +419,12 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                         R0h = sqrtf(Sh);
                         R0l = __fdiv_rn(__fadd_rn(__fmaf_rn(-R0h, R0h, Sh), Sl), 2.f * R0h);
                         const float inv = __frcp_rn(R0h);
-                        for (int d = 0; d < 3; ++d) Dn[d] = __fmul_rn(__fadd_rn(Dh[d], Dl[d]), inv);
+                        // unit vector D / |D| as a float pair (hi, lo)
+                        for (int d = 0; d < 3; ++d) {
+                            Dn[d] = __fmul_rn(__fadd_rn(Dh[d], Dl[d]), inv);
+                            const float res = __fsub_rn(__fadd_rn(__fmaf_rn(-Dn[d], R0h, Dh[d]), Dl[d]), __fmul_rn(Dn[d], R0l));
+                            Dnl[d] = __fmul_rn(res, inv);
+                        }
                     }
                     for (int base = K1; base <= K2; base += GP_KSLOT) {
                         const int k = base + ks;
@@ -243,7 +433,8 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                         const int pb = sp0[cbl], pe = sp0[cbl + 1];
                         // sums over the trial points: t_b = sum_y w_y lambda_b(y) psi / r, s~ = sum_y w_y psi~ / r
                         double t0 = 0.0, t1 = 0.0, t2 = 0.0, ts = 0.0;
-                        float f0 = 0.f, f1 = 0.f, f2 = 0.f, fs = 0.f;
+                        float f0 = 0.f, f1 = 0.f, f2 = 0.f, fs = 0.f;   // float pairs (f, fl)
+                        float f0l = 0.f, f1l = 0.f, f2l = 0.f, fsl = 0.f;
                         if (act) {
                             if constexpr (FP64) {
                                 const double ba = sa[cbl], bb = sb[cbl];
@@ -265,31 +456,13 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                                 }
                             } else {
                                 const float fa = (float)sa[cbl], fb = (float)sb[cbl];
-                                for (int y = 0; y < 7; ++y) {
-                                    const float *qy = g.dq32 + (sg * 7 + y) * 3;
-                                    const float e0 = ex[0] - qy[0], e1 = ex[1] - qy[1], e2 = ex[2] - qy[2];
-                                    // r - R0 = u + |e_perp|^2 / ((R0 + u) + r), u = D^.e
-                                    const float u = fmaf(Dn[0], e0, fmaf(Dn[1], e1, Dn[2] * e2));
-                                    const float ee = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-                                    const float ep = fmaxf(fmaf(-u, u, ee), 0.f);
-                                    const float r1 = sqrtf(fmaf(R0h, R0h, fmaf(2.f * R0h, u, ee)));
-                                    const float dl = u + ep / ((R0h + u) + r1);
-                                    const float s = R0l + dl;
-                                    const float rr = R0h + s;
-                                    if (!(rr > fa && rr < fb)) continue;
-                                    int p = pb;
-                                    while (p + 1 < pe && rr >= smeta[p + 1].x) ++p;
-                                    const float4 mt = smeta[p];  // (start, mid_h, mid_l, 2 / width)
-                                    const float x = ((R0h - mt.y) + (s - mt.z)) * mt.w;
-                                    float ps, pt;
-                                    g_cheb32(scoef + (size_t)p * 17, x, ps, pt);
-                                    const float ir = __frcp_rn(rr);
-                                    const float v = ps * ir, vt = pt * ir;
-                                    f0 = fmaf(A.gwh[3 * y], v, fmaf(A.gwl[3 * y], v, f0));
-                                    f1 = fmaf(A.gwh[3 * y + 1], v, fmaf(A.gwl[3 * y + 1], v, f1));
-                                    f2 = fmaf(A.gwh[3 * y + 2], v, fmaf(A.gwl[3 * y + 2], v, f2));
-                                    fs = fmaf(A.wwh[y], vt, fmaf(A.wwl[y], vt, fs));
-                                }
+                                const float4 *scf = scoef;
+                                const float4 *smt = smeta;
+                                float acc[8] = {f0, f0l, f1, f1l, f2, f2l, fs, fsl};
+                                g_far_group<4>(A, scf, smt, sg, 0, ex, Dn, Dnl, R0h, R0l, fa, fb, pb, pe, acc);
+                                g_far_group<3>(A, scf, smt, sg, 4, ex, Dn, Dnl, R0h, R0l, fa, fb, pb, pe, acc);
+                                f0 = acc[0]; f0l = acc[1]; f1 = acc[2]; f1l = acc[3];
+                                f2 = acc[4]; f2l = acc[5]; fs = acc[6]; fsl = acc[7];
                             }
                         }
                         // weighted by the test point: S_ab = sum_x w_x lambda_a(x) t_b, S~ = sum_x w_x s~
@@ -324,18 +497,34 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                                 dense[(l * M + j) * KW + slot] += L;
                             }
                         } else {
-                            float S[10];
+                            // S_ab = sum_x (w_x lambda_a(x)) t_b(x) and S~ in float pairs: products of
+                            // the (hi, lo) weights and the (hi, lo) trial sums, then a two-sum
+                            // reduction over the 8 lanes of the group
+                            float S[10], SL[10];
                             const int xx = xs < 7 ? xs : 0;
+                            const float th[3] = {f0, f1, f2}, tlo[3] = {f0l, f1l, f2l};
                             for (int a = 0; a < 3; ++a) {
                                 const float gh = xs < 7 ? A.gwh[3 * xx + a] : 0.f, gl = xs < 7 ? A.gwl[3 * xx + a] : 0.f;
-                                S[3 * a] = fmaf(gh, f0, gl * f0);
-                                S[3 * a + 1] = fmaf(gh, f1, gl * f1);
-                                S[3 * a + 2] = fmaf(gh, f2, gl * f2);
+                                for (int b = 0; b < 3; ++b) {
+                                    S[3 * a + b] = __fmul_rn(gh, th[b]);
+                                    SL[3 * a + b] = __fmaf_rn(gh, tlo[b], __fmaf_rn(gl, th[b], __fmaf_rn(gh, th[b], -S[3 * a + b])));
+                                }
                             }
-                            S[9] = xs < 7 ? fmaf(A.wwh[xx], fs, A.wwl[xx] * fs) : 0.f;
+                            {
+                                const float gh = xs < 7 ? A.wwh[xx] : 0.f, gl = xs < 7 ? A.wwl[xx] : 0.f;
+                                S[9] = __fmul_rn(gh, fs);
+                                SL[9] = __fmaf_rn(gh, fsl, __fmaf_rn(gl, fs, __fmaf_rn(gh, fs, -S[9])));
+                            }
 #pragma unroll
                             for (int o = 1; o < 8; o <<= 1)
-                                for (int q = 0; q < 10; ++q) S[q] += __shfl_xor_sync(0xffffffffu, S[q], o);
+                                for (int q = 0; q < 10; ++q) {
+                                    const float oh = __shfl_xor_sync(0xffffffffu, S[q], o);
+                                    const float ol = __shfl_xor_sync(0xffffffffu, SL[q], o);
+                                    float sh, se;
+                                    g_two_sum(S[q], oh, sh, se);
+                                    S[q] = sh;
+                                    SL[q] = __fadd_rn(__fadd_rn(SL[q], ol), se);
+                                }
                             // combination L_ab = |tau||sigma|/(4 pi) (n.n S_ab + curl_a.curl_b S~) in
                             // float-pair arithmetic from the FP32-pair geometry of both triangles
                             const float *gt = A.geoh + 16 * tau, *gs = A.geoh + 16 * sg;
@@ -378,6 +567,8 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                                 float ah, al, bh, bl, s, ee;
                                 g_ff_mul(nnh, nnl, S[e], ah, al);
                                 g_ff_mul(cch, ccl, S[9], bh, bl);
+                                al = __fmaf_rn(nnh, SL[e], al);
+                                bl = __fmaf_rn(cch, SL[9], bl);
                                 g_two_sum(ah, bh, s, ee);
                                 const float sl = __fadd_rn(ee, __fadd_rn(al, bl));
                                 const float Lh = __fmul_rn(sch, s);
@@ -390,8 +581,9 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                             }
                         }
                     }
+                  }
+                  __syncthreads();
                 }
-                __syncthreads();
             }
         }
     }
@@ -648,10 +840,10 @@ void launch_gcount(const GradedArgs &a, const int *cb2api, const int64_t *nbr_pt
 
 // ------------------------------------------------- quadrature point pairs
 __global__ void gcount_quad_kernel(const GradedArgs A, int npp0, int npp1, int npp2, int npp3, int64_t *partial) {
-    __shared__ int64_t red[256];
+    __shared__ int64_t red[256], redf[256];
     const Geo &g = A.g;
     const int64_t E = g.E, n = E * E;
-    int64_t acc = 0;
+    int64_t acc = 0, accf = 0;
     for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < n; id += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = id / E, s = id % E;
         int shared = 0;
@@ -668,14 +860,16 @@ __global__ void gcount_quad_kernel(const GradedArgs A, int npp0, int npp1, int n
         }
         const int npp = shared == 0 ? npp0 : (shared == 1 ? npp1 : (shared == 2 ? npp2 : npp3));
         acc += kept * npp;
+        if (shared == 0) accf += kept * npp;
     }
     red[threadIdx.x] = acc;
+    redf[threadIdx.x] = accf;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        if (threadIdx.x < s) { red[threadIdx.x] += red[threadIdx.x + s]; redf[threadIdx.x] += redf[threadIdx.x + s]; }
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (threadIdx.x == 0) { partial[blockIdx.x] = red[0]; partial[gridDim.x + blockIdx.x] = redf[0]; }
 }
 
 void launch_gcount_quad(const GradedArgs &a, int npp_far, const int *npp_near, int64_t *partial, int nblocks,
@@ -765,24 +959,30 @@ void launch_gfill(const GradedArgs &a, const int *cb2api, const int64_t *nbr_ptr
                                                             (float *)val_far, rp_near, off_near, col_near, val_near);
 }
 
-// FP32 coefficient layout of the far kernel: per panel 17 float4 =
-// (psi_n, psi~_n, psi_{n+1}, psi~_{n+1}), n = 0, 2, .., 32, entry 33 zero.
+// FP32 coefficient layout of the far kernel: per panel GC32 float4 = 17 x
+// (psi_n, psi~_n, psi_{n+1}, psi~_{n+1}), n = 0, 2, .., 32 (entry 33 zero),
+// then (lo_0, lo~_0, lo_1, lo~_1), (lo_2, lo~_2, lo_3, lo~_3) with
+// lo_n = c_n - (double)(float)c_n.
 __global__ void gcoef32_kernel(const double *coef, int npan, float *out) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= npan * 34) return;
-    const int p = id / 34, n = id % 34;
+    if (id >= npan * 38) return;
+    const int p = id / 38, n = id % 38;
     float a = 0.f, b = 0.f;
     if (n < NCHEB) {
         a = (float)coef[((size_t)p * NCHEB + n) * 2];
         b = (float)coef[((size_t)p * NCHEB + n) * 2 + 1];
+    } else if (n >= 34) {
+        const double ca = coef[((size_t)p * NCHEB + (n - 34)) * 2], cb = coef[((size_t)p * NCHEB + (n - 34)) * 2 + 1];
+        a = (float)(ca - (double)(float)ca);
+        b = (float)(cb - (double)(float)cb);
     }
-    out[(size_t)p * 68 + 2 * n] = a;
-    out[(size_t)p * 68 + 2 * n + 1] = b;
+    out[(size_t)p * 4 * GC32 + 2 * n] = a;
+    out[(size_t)p * 4 * GC32 + 2 * n + 1] = b;
 }
 
 void launch_gcoef32(const double *coef, int npan, float *out, cudaStream_t st) {
     if (npan <= 0) return;
-    gcoef32_kernel<<<(npan * 34 + 255) / 256, 256, 0, st>>>(coef, npan, out);
+    gcoef32_kernel<<<(npan * 38 + 255) / 256, 256, 0, st>>>(coef, npan, out);
 }
 
 }  // namespace tdbem

@@ -364,7 +364,8 @@ void launch_gcount(const GradedArgs &a, const int *cb2api, const int64_t *nbr_pt
                    int64_t *cnt_far, int64_t *cnt_near, cudaStream_t st);
 // vertex-pair Dmin / Dmax and per-CTA maxima of Dmax - Dmin (partial, nblocks entries)
 void launch_gvertex(const GradedArgs &a, double *vmin, double *vmax, double *partial, int nblocks, cudaStream_t st);
-// quadrature point pairs x kept blocks over all element pairs (per-CTA partial sums)
+// quadrature point pairs x kept blocks over all element pairs (per-CTA partial
+// sums: partial[0, nblocks) all pairs, partial[nblocks, 2 nblocks) far pairs)
 void launch_gcount_quad(const GradedArgs &a, int npp_far, const int *npp_near, int64_t *partial, int nblocks,
                         cudaStream_t st);
 // CSR fill of the blocks of batch columns [a.i0, a.i1)

@@ -180,6 +180,8 @@ def workload(name: str) -> Workload:
                   N=65, dt=0.0625, T=4
     torus8192g  : torus R=1 r=0.4 (128x32 quads, 8192 / 4096), graded grid of
                   96 steps, ratio 1.02, on [0, 6]
+    torus2048g  : the same torus and grid on 64x16 quads (2048 / 1024), a
+                  small case of the same kernels (profiling, parity)
     sphere20480 : icosphere level 5 (20480 / 10242), N=129, dt=0.05, T=6.4
     """
     if name == "sphere320":
@@ -190,6 +192,9 @@ def workload(name: str) -> Workload:
         return Workload(name, jitter(V, F, 0.01, 0), F, equidistant_grid(65, 4.0), True)
     if name == "torus8192g":
         V, F = torus(1.0, 0.4, 128, 32)
+        return Workload(name, V, F, graded_grid(96, 1.02, 6.0), False)
+    if name == "torus2048g":
+        V, F = torus(1.0, 0.4, 64, 16)
         return Workload(name, V, F, graded_grid(96, 1.02, 6.0), False)
     if name == "sphere20480":
         V, F = icosphere(5)

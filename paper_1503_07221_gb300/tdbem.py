@@ -32,7 +32,7 @@ class TdbemError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("near_order", C.c_int32), ("cheb_degree", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("staging_mb", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Stats(C.Structure):
@@ -40,7 +40,7 @@ class Stats(C.Structure):
                 ("far_pairs", C.c_int64), ("near_pairs", C.c_int64), ("quad_points", C.c_int64),
                 ("ms_total", C.c_double), ("ms_pattern", C.c_double), ("ms_far", C.c_double),
                 ("ms_near", C.c_double), ("ms_extract", C.c_double), ("kernel_launches", C.c_int64),
-                ("graph_replays", C.c_int64), ("matvec_variant", C.c_int64)]
+                ("graph_replays", C.c_int64), ("matvec_variant", C.c_int64), ("quad_points_far", C.c_int64)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -170,10 +170,11 @@ class TimeGrid:
 class Assembler:
     """Unique blocks of the block-Hessenberg system of one mesh and time grid."""
 
-    def __init__(self, mesh: Mesh, grid: TimeGrid, precision=PREC_MIXED, near_order=4, stream=None):
+    def __init__(self, mesh: Mesh, grid: TimeGrid, precision=PREC_MIXED, near_order=4, stream=None, staging_mb=0):
         o = Opts()
         o.precision = precision
         o.near_order = near_order
+        o.staging_mb = staging_mb
         o.cheb_degree = 32
         h = C.c_void_p()
         _check(lib().tdbem_assembler_create(mesh.h, grid.h, C.byref(o), C.c_void_p(_stream(stream)), C.byref(h)))

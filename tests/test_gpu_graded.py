@@ -129,15 +129,48 @@ def test_graded_deterministic(td):
 
 def test_torus8192_graded_fullsize(td):
     """The batched uneven-block workload at full size (torus 8192 triangles,
-    96 graded steps of ratio 1.02 on [0, 6], mixed precision): every block's
-    pattern on three sampled rows, values of all blocks on those rows."""
+    96 graded steps of ratio 1.02 on [0, 6], mixed precision), in the launch
+    configuration bench.py times: row lengths of every block on 32 sampled
+    rows; columns and values of 120 sampled blocks (seeded) on 3 rows."""
     w = inputs.workload("torus8192g")
-    rows = np.array([5, 1111, 3333])
-    asm, orc, errs = _compare(td, w.verts, w.tris, w.t, 1, rows=rows)
-    rel, absmax = _worst(errs)
+    rng = np.random.default_rng(0)
+    from oracle.oracle import Oracle
+    asm = td.Assembler(td.Mesh(w.verts, w.tris), td.TimeGrid(w.t), precision=1)
+    asm.assemble()
     st = asm.stats()
-    print("torus8192g mixed: %d blocks, nnz %d, worst rel %.3e at %s, median %.3e, abs %.3e, %.1f ms"
+    orc = Oracle(w.verts, w.tris, w.t, equidistant=False, psi_mode="interp")
+    ob = orc.blocks()
+    assert [(b[0], b[1]) for b in ob] == asm.blocks()
+    nb, M = len(ob), w.M
+    crow = np.sort(rng.choice(M, size=32, replace=False))
+    cnt = orc.pattern_counts(crow, np.arange(nb))
+    for b in range(nb):
+        rp = asm.block_csr_torch(b, td.FAR)[0].cpu().numpy()
+        assert np.array_equal(rp[crow + 1] - rp[crow], cnt[b]), "row lengths of block %d" % b
+    rows = np.array([5, 1111, 3333])
+    blocks = np.sort(rng.choice(nb, size=120, replace=False))
+    res = orc.assemble_rows(rows, blocks)
+    errs = []
+    for b in blocks:
+        b = int(b)
+        rp, col, val = asm.block_csr_torch(b, td.FAR)
+        rpn, coln, valn = asm.block_csr_torch(b, td.NEAR)
+        rp, rpn = rp.cpu().numpy(), rpn.cpu().numpy()
+        num = den = 0.0
+        for r, (c, f, n) in enumerate(res[b]):
+            l = rows[r]
+            gc = col[rp[l]:rp[l + 1]].cpu().numpy()
+            assert np.array_equal(c, gc), "pattern block %d row %d" % (b, l)
+            got = val[rp[l]:rp[l + 1]].double().cpu().numpy()
+            nc = coln[rpn[l]:rpn[l + 1]].cpu().numpy()
+            got[np.searchsorted(c, nc)] += valn[rpn[l]:rpn[l + 1]].cpu().numpy()
+            num += np.sum((got - (f + n)) ** 2)
+            den += np.sum((f + n) ** 2)
+        errs.append((np.sqrt(num / den) if den > 0 else np.sqrt(num), b, ob[b][:2], np.sqrt(den)))
+    rel, absmax = _worst(errs)
+    print("torus8192g mixed: %d blocks, nnz %d, worst rel %.3e at %s, median %.3e, abs %.3e, %.1f ms "
+          "(pattern %.1f, far %.1f, near %.1f, extract %.1f)"
           % (st["n_blocks"], st["nnz"], rel[0], rel[2], float(np.median([e[0] for e in errs])), absmax,
-             st["ms_total"]))
+             st["ms_total"], st["ms_pattern"], st["ms_far"], st["ms_near"], st["ms_extract"]))
     assert rel[0] < TOL[1], rel
     assert absmax < TOL[1], absmax
