@@ -161,6 +161,22 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the job takes as long as its slowest
+    replica); x unchanged without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job rate: the units every replica processed over the slowest time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def far_flops(st):
     # algorithmic FP32 work of the far kernel per far point pair: distance
     # and Chebyshev argument (~14 FMA-equivalents), T_n recurrence (31 FMA),
@@ -239,13 +255,11 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     mv_ms = float(np.mean([a.elapsed_time(b) for a, b in mv_ev])) / max(args.matvecs, 1)
     if dist:
-        tm = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ms = float(tm.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     st = asm.stats()
     nnz = st["nnz"]
-    value = nnz * world / (ms * 1e-3)
-    qps = st["quad_points"] * world / (ms * 1e-3)
+    value = job_throughput(nnz, world, ms)
+    qps = job_throughput(st["quad_points"], world, ms)
     nb = st["n_blocks"]
     launches_per_step = st["kernel_launches"] + 2 * args.matvecs  # transpose + product per matvec
     # matvec work: every stored entry times the number of block positions that reuse its block

@@ -235,30 +235,36 @@ __device__ __forceinline__ void g_ff_acc(float &h, float &l, float gh, float gl,
     l = __fadd_rn(l, __fadd_rn(e, pe));
 }
 
+// r - R0h of the point pair (x, y) of one element pair as (u, sl), u the
+// leading part: D^.e with D^ = (c_tau - c_sigma)/|D| and e the difference of
+// the FP32 offsets from the centroids, both as float pairs; sl = R0l + the
+// small terms, with r - R0 = u + |e_perp|^2 / ((R0 + u) + r)
+__device__ __forceinline__ float2 g_dist(const float *qx, const float *qy, const float (&Dn)[3], const float (&Dnl)[3],
+                                         float R0h, float R0l) {
+    float e0, e1, e2, l0, l1, l2;
+    g_two_sum(qx[0], -qy[0], e0, l0);
+    g_two_sum(qx[1], -qy[1], e1, l1);
+    g_two_sum(qx[2], -qy[2], e2, l2);
+    const float u = fmaf(Dn[0], e0, fmaf(Dn[1], e1, Dn[2] * e2));
+    const float ul = fmaf(Dn[0], l0, fmaf(Dn[1], l1, fmaf(Dn[2], l2, fmaf(Dnl[0], e0, fmaf(Dnl[1], e1, Dnl[2] * e2)))));
+    const float ee = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+    const float ep = fmaxf(fmaf(-u, u, ee), 0.f);
+    const float r1 = sqrtf(fmaf(R0h, R0h, fmaf(2.f * R0h, u, ee)));
+    const float q2 = ep / ((R0h + u) + r1);
+    return make_float2(u, R0l + ul + q2);
+}
+
 template <int NC>
-__device__ __forceinline__ void g_far_group(const GradedArgs &A, const float4 *scoef, const float4 *smeta, int64_t sg,
-                                            int y0, const float (&ex)[3], const float (&Dn)[3], const float (&Dnl)[3],
-                                            float R0h, float R0l, float fa, float fb, int pb, int pe,
+__device__ __forceinline__ void g_far_group(const GradedArgs &A, const float4 *scoef, const float4 *smeta,
+                                            const float2 *dist, int y0, float R0h, float fa, float fb, int pb, int pe,
                                             float (&acc)[8]) {
     float x[NC], ir[NC], ps[NC], pt[NC];
     bool in[NC];
     const float4 *cf[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float *qy = A.g.dq32 + (sg * 7 + y0 + c) * 3;
-        // e = x - y offsets, exactly as a float pair; u = D^.e with D^ a float pair
-        float e0, e1, e2, l0, l1, l2;
-        g_two_sum(ex[0], -qy[0], e0, l0);
-        g_two_sum(ex[1], -qy[1], e1, l1);
-        g_two_sum(ex[2], -qy[2], e2, l2);
-        const float u = fmaf(Dn[0], e0, fmaf(Dn[1], e1, Dn[2] * e2));
-        const float ul = fmaf(Dn[0], l0, fmaf(Dn[1], l1, fmaf(Dn[2], l2, fmaf(Dnl[0], e0, fmaf(Dnl[1], e1, Dnl[2] * e2)))));
-        // r - R0 = u + |e_perp|^2 / ((R0 + u) + r)
-        const float ee = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-        const float ep = fmaxf(fmaf(-u, u, ee), 0.f);
-        const float r1 = sqrtf(fmaf(R0h, R0h, fmaf(2.f * R0h, u, ee)));
-        const float q2 = ep / ((R0h + u) + r1);
-        const float sl = R0l + ul + q2;  // small terms of r - R0h
+        const float2 du = dist[y0 + c];
+        const float u = du.x, sl = du.y;
         const float s = u + sl;
         const float rr = R0h + s;
         in[c] = rr > fa && rr < fb;
@@ -307,6 +313,7 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
     float4 *scoef = smeta + A.maxpan;
     __shared__ int2 s_list[GF_LIST];  // kept far pairs: (sigma, K1 << 16 | K2)
     __shared__ int s_cnt, s_next;
+    __shared__ float2 s_dist[GF_WARPS][56];  // per warp: (u, sl) of the 49 point pairs, index 7 x + y
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int xs = lane & 7, ks = lane >> 3;
     const Geo &g = A.g;
@@ -425,6 +432,15 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                             const float res = __fsub_rn(__fadd_rn(__fmaf_rn(-Dn[d], R0h, Dh[d]), Dl[d]), __fmul_rn(Dn[d], R0l));
                             Dnl[d] = __fmul_rn(res, inv);
                         }
+                        // the 49 point-pair distances, once per element pair (every block
+                        // round of the warp reads them)
+                        __syncwarp();
+                        for (int it = lane; it < 49; it += 32) {
+                            const int px = it / 7, py = it % 7;
+                            s_dist[w][it] = g_dist(g.dq32 + (tau * 7 + px) * 3, g.dq32 + (sg * 7 + py) * 3, Dn, Dnl,
+                                                   R0h, R0l);
+                        }
+                        __syncwarp();
                     }
                     for (int base = K1; base <= K2; base += GP_KSLOT) {
                         const int k = base + ks;
@@ -459,8 +475,9 @@ __global__ void __launch_bounds__(GF_WARPS * 32, 1) gfar_kernel(const GradedArgs
                                 const float4 *scf = scoef;
                                 const float4 *smt = smeta;
                                 float acc[8] = {f0, f0l, f1, f1l, f2, f2l, fs, fsl};
-                                g_far_group<4>(A, scf, smt, sg, 0, ex, Dn, Dnl, R0h, R0l, fa, fb, pb, pe, acc);
-                                g_far_group<3>(A, scf, smt, sg, 4, ex, Dn, Dnl, R0h, R0l, fa, fb, pb, pe, acc);
+                                const float2 *dist = &s_dist[w][7 * xs];
+                                g_far_group<4>(A, scf, smt, dist, 0, R0h, fa, fb, pb, pe, acc);
+                                g_far_group<3>(A, scf, smt, dist, 4, R0h, fa, fb, pb, pe, acc);
                                 f0 = acc[0]; f0l = acc[1]; f1 = acc[2]; f1l = acc[3];
                                 f2 = acc[4]; f2l = acc[5]; fs = acc[6]; fsl = acc[7];
                             }
