@@ -21,20 +21,30 @@ i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 
 
+def compile_library(src: str, out: str) -> str:
+    """gcc -O2 -fopenmp of one oracle source file into a shared library."""
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", out, src, "-lm"])
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2 -fopenmp) next to its source."""
+    """Compile the oracle next to its source (when the source is newer)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        compile_library(_SRC, tmp)
         os.replace(tmp, _LIB)
     return _LIB
 
 
 def lib():
+    """The oracle library. TDBEM_ORACLE_LIB names a prebuilt copy to load
+    instead (the mutation tests point it at a copy with a planted mistake)."""
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
+        path = os.environ.get("TDBEM_ORACLE_LIB")
+        if not path:
+            path = build()
+        L = C.CDLL(path)
         L.or_create.restype = C.c_void_p
         L.or_create.argtypes = [f64p, C.c_int64, i32p, C.c_int64, f64p, C.c_int64,
                                 C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]

@@ -174,6 +174,15 @@ def test_triangle_distance_bounds():
     ot = Oracle(Vt, Ft, inputs.equidistant_grid(5, 1.0), psi_mode="direct")
     dmin, dmax = ot.tri_bounds(0, 1)
     assert abs(dmin - 0.3) < 1e-15 and abs(dmax - math.sqrt(2 + 0.09)) < 1e-15
+    # exact value attained only between edge interiors: the x-axis edge of a
+    # triangle that drops steeply away (z = 10 y, y <= 0) and the crossing
+    # edge x = 0, z = 0.3 of a vertical triangle above it; every vertex-face
+    # foot point falls outside the other triangle, so dmin = 0.3 comes from
+    # the segment-segment distance alone
+    Ve = np.array([[-1, 0, 0], [1, 0, 0], [0, -0.1, -1], [0, -1, 0.3], [0, 1, 0.3], [0, 0, 1.3]], float)
+    oe = Oracle(Ve, Ft, inputs.equidistant_grid(5, 1.0), psi_mode="direct")
+    for s, q in [(0, 1), (1, 0)]:
+        assert abs(oe.tri_bounds(s, q)[0] - 0.3) < 1e-15
 
 
 # ------------------------------------------------------------ block list --
@@ -290,6 +299,32 @@ def test_pattern_matches_sampled_distances():
                     assert j in row
                 if lo[l, j] > bb + 0.05 or hi[l, j] < a - 1e-9:
                     assert j not in row
+
+
+def test_pattern_counts_on_fine_grid():
+    # the same criterion with supports (4 dt = 0.16) narrow against the
+    # distance range of the stars [0, 1]: every row length lies between the
+    # number of columns that certainly qualify (sampled star distances inside
+    # the support by a margin; the sampled maximum is exact, since it sits at
+    # vertices, the sampled minimum is an upper bound) and the number that
+    # possibly qualify
+    V, F = inputs.tiny_meshes()["icosa"]
+    t = inputs.equidistant_grid(41, 1.6)
+    o = Oracle(V, F, t, equidistant=False, psi_mode="direct")
+    rng = np.random.default_rng(3)
+    u = np.vstack([rng.dirichlet([1, 1, 1], size=200), np.eye(3)])
+    stars = {v: np.vstack([u @ V[F[e]] for e in range(F.shape[0]) if v in F[e]]) for v in range(o.M)}
+    lo = np.zeros((o.M, o.M)); hi = np.zeros((o.M, o.M))
+    for l in range(o.M):
+        for j in range(o.M):
+            D = np.linalg.norm(stars[l][:, None] - stars[j][None], axis=2)
+            lo[l, j], hi[l, j] = D.min(), D.max()
+    err = 0.06  # sampling error of the minimum, well above what 200 points leave
+    counts = o.pattern_counts(np.arange(o.M), np.arange(o.num_blocks()))
+    for b, (kb, ib, m2, m1, a, bb) in enumerate(o.blocks()):
+        sure = ((lo < bb - 1e-9) & (hi > a + 1e-9)).sum(axis=1)
+        maybe = ((lo - err < bb) & (hi > a - 1e-9)).sum(axis=1)
+        assert (sure <= counts[b]).all() and (counts[b] <= maybe).all(), (kb, ib)
 
 
 def test_toeplitz_block_reuse():
