@@ -34,6 +34,16 @@ def test_reduced_matvec_equals_full_block_matrix():
         assert np.linalg.norm(z) > 0
 
 
+def test_matvec_equals_dense_product():
+    # the product loop against the dense space-time matrix laid out block by
+    # block (row block k, column block i) from every directly assembled block
+    _, full = _pair(9, 2.0)
+    x = _x(full.N, full.M, seed=5)
+    y = full.hessenberg_apply(x)
+    z = (full.full_matrix() @ x.ravel()).reshape(full.N, full.M)
+    assert np.linalg.norm(y - z) <= 1e-13 * np.linalg.norm(z)
+
+
 def test_diam_cut_is_active_on_long_grid():
     o, full = _pair(17, 6.4)
     lags = {b[0] - b[1] for b in full.blocks()}

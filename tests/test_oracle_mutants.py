@@ -1,11 +1,14 @@
 """The oracle's pins catch plausible mistakes: each case below plants one
 mistake (a wrong sign, index, operand, factor or a dropped term) in a
-temporary copy of the oracle's C source, builds it, and runs the pin tests
-named for it against that copy (TDBEM_ORACLE_LIB), which must fail. The
-committed oracle is never modified; everything runs on the CPU.
+temporary copy of one oracle source file and runs the pin tests named for it
+against that copy, which must fail. A C mistake is built into a separate
+library that the pins load through TDBEM_ORACLE_LIB; a Python mistake goes
+into a copy of the `oracle` package placed first on the import path of the
+pin run. The committed oracle is never modified; everything runs on the CPU.
 """
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 
@@ -14,9 +17,10 @@ import pytest
 from oracle import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-T, S, R = "tests/test_oracle_time.py", "tests/test_oracle_space.py", "tests/test_oracle_radial.py"
+T, S = "tests/test_oracle_time.py", "tests/test_oracle_space.py"
+MV, RHS, KR = "tests/test_oracle_matvec.py", "tests/test_oracle_rhs.py", "tests/test_oracle_krylov.py"
 
-# name: (exact source text, planted replacement, pin tests that must fail)
+# name: (exact source text, planted replacement, pin tests that must fail), in tdbem_oracle.c
 MUTANTS = {
     "step f'' sign": ("(x - 2.0 * u)", "(2.0 * u - x)", [T + "::test_basis_derivatives_fd"]),
     "psi takes bdot_i for bddot_i": ("s0 += wt * bi[2] * bk[1];", "s0 += wt * bi[1] * bk[1];",
@@ -62,6 +66,40 @@ MUTANTS = {
 }
 
 
+# the same for the Python parts: (file in oracle/, text, replacement, pins)
+PY_MUTANTS = {
+    "reused block of the wrong lag": ("oracle.py", "key = (d + 1, 1)", "key = (d, 1)",
+                                      [MV + "::test_reduced_matvec_equals_full_block_matrix"]),
+    "superdiagonal from the diagonal block": ("oracle.py", "key = (1, 2)", "key = (1, 1)",
+                                              [MV + "::test_reduced_matvec_equals_full_block_matrix"]),
+    "matvec reads x of the test index": ("oracle.py", "np.dot(f + n, x[ib, c])", "np.dot(f + n, x[kb, c])",
+                                         [MV + "::test_matvec_equals_dense_product"]),
+    "right-hand side tested with b for bdot": ("oracle.py", "bd = self.basis(k, 0, s_n)[:, 1]",
+                                               "bd = self.basis(k, 0, s_n)[:, 0]",
+                                               [RHS + "::test_rhs_sphere_n0_closed_form"]),
+    "right-hand side weights against reversed points": ("oracle.py", "w7[None, :, None] * bary[None, :, :]",
+                                                        "w7[None, :, None] * bary[None, ::-1, :]",
+                                                        [RHS + "::test_rhs_plane_wave_brute_force"]),
+    "Gram-Schmidt sign": ("krylov.py", "w = w - H[i, j] * V[i]", "w = w + H[i, j] * V[i]",
+                          [KR + "::test_gmres_iterate_is_krylov_minimal_residual"]),
+    "flexible update with V for Z": ("krylov.py", "x = x + Z[:jdone].T @ y", "x = x + V[:jdone].T @ y",
+                                     [KR + "::test_fixed_preconditioner_is_right_preconditioned_gmres"]),
+    "coupling block sign in M^-1": ("krylov.py", "t = r[n1:] - self._sub(h, hi, lo, h) @ y1",
+                                    "t = r[n1:] + self._sub(h, hi, lo, h) @ y1",
+                                    [KR + "::test_exact_inner_solves_invert_block_triangular_M"]),
+    "split point rounded down": ("krylov.py", "h = lo + (hi - lo + 1) // 2", "h = lo + (hi - lo) // 2",
+                                 [KR + "::test_exact_inner_solves_invert_block_triangular_M"]),
+}
+
+
+def _pins(nodes, env, cwd):
+    env = dict(env, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-rf", "-p", "no:cacheprovider", *nodes],
+                       env=env, cwd=cwd, capture_output=True, text=True, timeout=600)
+    failed = [line for line in r.stdout.splitlines() if line.startswith("FAILED")]
+    return r.returncode, failed, r.stdout[-2000:]
+
+
 def _run(name, tmp):
     old, new, nodes = MUTANTS[name]
     src = open(O._SRC).read()
@@ -71,17 +109,31 @@ def _run(name, tmp):
     with open(path, "w") as f:
         f.write(src.replace(old, new))
     lib = O.compile_library(path, os.path.join(tmp, tag + ".so"))
-    env = dict(os.environ, TDBEM_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-rf", "-p", "no:cacheprovider", *nodes],
-                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
-    failed = [line for line in r.stdout.splitlines() if line.startswith("FAILED")]
-    return r.returncode, failed, r.stdout[-2000:]
+    return _pins(nodes, dict(os.environ, TDBEM_ORACLE_LIB=lib), ROOT)
+
+
+def _run_py(name, tmp, lib):
+    fname, old, new, nodes = PY_MUTANTS[name]
+    pkg = os.path.join(tmp, "p%02d" % sorted(PY_MUTANTS).index(name))
+    os.makedirs(os.path.join(pkg, "oracle"))
+    for f in ("__init__.py", "oracle.py", "krylov.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(pkg, "oracle", f))
+    target = os.path.join(pkg, "oracle", fname)
+    src = open(target).read()
+    assert src.count(old) == 1, "%s: the planted text must occur once in oracle/%s" % (name, fname)
+    with open(target, "w") as f:
+        f.write(src.replace(old, new))
+    # the copy comes first on the path (cwd); the repository follows for the rest
+    env = dict(os.environ, TDBEM_ORACLE_LIB=lib, PYTHONPATH=os.pathsep.join([pkg, ROOT]))
+    return _pins([os.path.join(ROOT, n) for n in nodes], env, pkg)
 
 
 @pytest.mark.slow
 def test_pins_catch_planted_mistakes(tmp_path):
-    names = sorted(MUTANTS)
+    lib = O.build()
+    jobs = [("c", n) for n in sorted(MUTANTS)] + [("py", n) for n in sorted(PY_MUTANTS)]
+    run = lambda j: _run(j[1], str(tmp_path)) if j[0] == "c" else _run_py(j[1], str(tmp_path), lib)
     with cf.ThreadPoolExecutor(max_workers=4) as ex:
-        res = dict(zip(names, ex.map(lambda n: _run(n, str(tmp_path)), names)))
+        res = dict(zip(jobs, ex.map(run, jobs)))
     missed = {n: out for n, (rc, failed, out) in res.items() if rc != 1 or not failed}
     assert not missed, "pins that did not catch their planted mistake: %s" % missed
