@@ -35,6 +35,13 @@ MUTANTS = {
                                  [T + "::test_legendre_factor"]),
     "psi split point dropped": ("if (ib > 0 && ib < P->N - 1) cand[nc++] = P->t[ib] + r;", ";",
                                 [T + "::test_quadrature_refinement_converged"]),
+    "interpolant end weights not halved": ("if (j == 0 || j == I->n) wj *= 0.5;", ";",
+                                           [T + "::test_interpolant_matches_direct"]),
+    "interpolant panel split dropped": ("if (d > a && d < b) br[nbr++] = d;", "if (d > a && d < b && x != 1) br[nbr++] = d;",
+                                        [T + "::test_interpolant_matches_direct"]),
+    "interpolant argument mirrored": ("double x = (2.0 * r - ea - eb) / (eb - ea);",
+                                      "double x = (ea + eb - 2.0 * r) / (eb - ea);",
+                                      [T + "::test_interpolant_matches_direct"]),
     "psi support end": ("*b = tr(P, kb) - tl(P, ib);", "*b = tr(P, kb) - tr(P, ib);",
                         [S + "::test_unique_block_list_equidistant"]),
     "block A_{2,3} dropped": ("want[1 * N + 2] = 1;", "(void)0;", [S + "::test_unique_block_list_equidistant"]),

@@ -210,9 +210,11 @@ def test_quadrature_refinement_converged():
         assert np.abs(a - b).max() <= 1e-12 * max(np.abs(b).max(), 1e-300), (kb, ib)
 
 
-def test_interpolant_matches_direct():
+@pytest.mark.parametrize("t", [inputs.equidistant_grid(9, 2.0), inputs.graded_grid(8, 1.3, 2.0)],
+                         ids=["eq", "graded"])
+def test_interpolant_matches_direct(t):
+    # on the graded grid the panel breakpoints t_{k-a} - t_{i-b} are all distinct
     V, F = inputs.tiny_meshes()["octa"]
-    t = inputs.equidistant_grid(9, 2.0)
     od = Oracle(V, F, t, equidistant=False, psi_mode="direct")
     oi = Oracle(V, F, t, equidistant=False, psi_mode="interp")
     r = np.random.default_rng(0).uniform(0.0, 2.0, 400)
