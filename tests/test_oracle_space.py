@@ -348,6 +348,27 @@ def test_toeplitz_block_reuse():
     assert np.linalg.norm(A - B) > 1e-3 * np.linalg.norm(A)
 
 
+def test_order_symmetry_of_inner_blocks():
+    # Eq. relationAblock (p >= 1): for inner k~, i~ the block of test order
+    # m2 and trial order m1 is (-1)^(m1+m2) times the block with the orders
+    # swapped (from Eq. symmetryXi and Eq. symmetryXip); a first-column block
+    # has no such relation (negative control)
+    V, F = inputs.icosphere(1)
+    t = inputs.equidistant_grid(9, 2.0)
+    o = Oracle(V, F, t, p=2, equidistant=False, psi_mode="interp")
+    idx = {b[:4]: n for n, b in enumerate(o.blocks())}
+    cases = [((4, 3), 0, 1), ((4, 3), 1, 2), ((5, 2), 0, 2), ((3, 4), 0, 1)]
+    blks = sorted({idx[(k, i, a, b)] for (k, i), a, b in cases} | {idx[(k, i, b, a)] for (k, i), a, b in cases}
+                  | {idx[(4, 0, 0, 1)], idx[(4, 0, 1, 0)]})
+    D = _dense(o, blks)
+    for (k, i), a, b in cases:
+        A = sum(D[idx[(k, i, a, b)]]); B = sum(D[idx[(k, i, b, a)]])
+        assert np.linalg.norm(A) > 0
+        assert np.linalg.norm(A - (-1) ** (a + b) * B) <= 1e-10 * np.linalg.norm(A), (k, i, a, b)
+    A = sum(D[idx[(4, 0, 0, 1)]]); B = sum(D[idx[(4, 0, 1, 0)]])
+    assert np.linalg.norm(A + B) > 1e-2 * np.linalg.norm(A)
+
+
 def test_far_and_near_quadrature_convergence():
     V, F = inputs.tiny_meshes()["icosa"]
     o = Oracle(V, F, inputs.equidistant_grid(9, 2.0), equidistant=False, psi_mode="interp")
