@@ -269,9 +269,10 @@ class Oracle:
             out[int(b)] = lst
         return out
 
-    def block_source(self, kb, ib):
+    def block_source(self, kb, ib, m2=0, m1=0):
         """Listed block that holds block (kb, ib) of the whole matrix
-        (0-based time indices, Eq. Apartitioned), or None for a zero block.
+        (0-based time indices, Eq. Apartitioned) for test order m2 and trial
+        order m1, or None for a zero block.
 
         Without the equidistant reduction every nonzero block is listed. On an
         equidistant grid the list holds the first two block columns, the last
@@ -281,7 +282,7 @@ class Oracle:
         is zero above that (Hessenberg, Eq. Apartitioned). Blocks cut by the
         diam criterion (Sec. 5.1) are absent from the list and zero."""
         if not hasattr(self, "_bidx"):
-            self._bidx = {(b[0], b[1]): n for n, b in enumerate(self.blocks())}
+            self._bidx = {b[:4]: n for n, b in enumerate(self.blocks())}
         N = self.N
         key = (kb, ib)
         if self.equidistant and 1 <= kb <= N - 2 and 1 <= ib <= N - 2:
@@ -292,27 +293,36 @@ class Oracle:
                 key = (1, 2)
             else:
                 return None
-        return self._bidx.get(key)
+        return self._bidx.get(key + (m2, m1))
+
+    @property
+    def L(self):
+        """Number of time basis functions, N (p + 1) (Sec. 3)."""
+        return self.N * (self.p + 1)
 
     def hessenberg_apply(self, x, rows=None):
         """y = A x for the whole space-time system (Eq. Apartitioned): x and y
-        are (N, M) arrays, x[i] the coefficients of trial time basis function
-        i, y[k] the result on test function k. With `rows` given, only the
-        columns y[:, rows] are computed (the rest stay zero). Every block
-        comes from the listed blocks through block_source."""
+        are (L, M) arrays, L = N (p + 1), row kb (p + 1) + m the coefficients
+        of time basis function b_{kb, m} (the numbering of Sec. 3 with 0-based
+        indices; for p = 0 row k is time function k): x of the trial, y of
+        the test functions. With `rows` given, only the columns y[:, rows]
+        are computed (the rest stay zero). Every block comes from the listed
+        blocks through block_source."""
         x = np.asarray(x, dtype=np.float64)
-        N, M = self.N, self.M
+        N, M, P = self.N, self.M, self.p + 1
         rows = np.arange(M) if rows is None else np.asarray(rows, dtype=np.int64)
         nb = self.num_blocks()
         R = self.assemble_rows(rows, np.arange(nb))
-        y = np.zeros((N, M))
+        y = np.zeros((N * P, M))
         for kb in range(N):
             for ib in range(N):
-                b = self.block_source(kb, ib)
-                if b is None:
-                    continue
-                for r, (c, f, n) in enumerate(R[b]):
-                    y[kb, rows[r]] += np.dot(f + n, x[ib, c])
+                for m2 in range(P):
+                    for m1 in range(P):
+                        b = self.block_source(kb, ib, m2, m1)
+                        if b is None:
+                            continue
+                        for r, (c, f, n) in enumerate(R[b]):
+                            y[kb * P + m2, rows[r]] += np.dot(f + n, x[ib * P + m1, c])
         return y
 
     def rhs(self, kind, params=(), nt=16, sub=4):
@@ -321,7 +331,7 @@ class Oracle:
         partitioned system), as an (N, M) array: the 7-point rule on every
         triangle in space, composite Gauss-Legendre in time on every
         [t_j, t_{j+1}] (the breakpoints of every bdot_k), `sub` panels of
-        `nt` points each."""
+        `nt` points each. Shape (L, M), row k (p + 1) + m for b_{k, m}."""
         bary, w7 = rule7()
         P = self.V[self.F]                                     # (E, 3, 3)
         X = np.einsum("pa,eaj->epj", bary, P)                  # (E, 7, 3)
@@ -340,20 +350,23 @@ class Oracle:
         s_n = np.concatenate(s_list)
         w_n = np.concatenate(w_list)
         G = g_data(kind, params, X, np.repeat(nrm[:, None, :], 7, axis=1), s_n)  # (E, 7, Ns)
-        out = np.zeros((self.N, self.M))
+        P = self.p + 1
+        out = np.zeros((self.N * P, self.M))
         coef = area[:, None, None] * w7[None, :, None] * bary[None, :, :]     # (E, 7, 3)
         for k in range(self.N):
-            bd = self.basis(k, 0, s_n)[:, 1]
-            H = G @ (w_n * bd)                                  # (E, 7)
-            contrib = np.einsum("ep,epa->ea", H, coef)          # (E, 3)
-            np.add.at(out[k], self.F.ravel(), contrib.ravel())
+            for m in range(P):
+                bd = self.basis(k, m, s_n)[:, 1]
+                H = G @ (w_n * bd)                              # (E, 7)
+                contrib = np.einsum("ep,epa->ea", H, coef)      # (E, 3)
+                np.add.at(out[k * P + m], self.F.ravel(), contrib.ravel())
         return out
 
     def full_matrix(self):
-        """The whole space-time matrix (N M x N M) of Eq. Apartitioned, block
-        (k, i) at rows k M.., columns i M.., from the listed blocks through
-        block_source (small cases only)."""
-        N, M = self.N, self.M
+        """The whole space-time matrix (L M x L M, L = N (p + 1)) of Eq.
+        Apartitioned, block (k, i) of orders (m2, m1) at rows
+        (k (p + 1) + m2) M.., columns (i (p + 1) + m1) M.., from the listed
+        blocks through block_source (small cases only)."""
+        N, M, P = self.N, self.M, self.p + 1
         nb = self.num_blocks()
         R = self.assemble_rows(np.arange(M), np.arange(nb))
         D = []
@@ -362,18 +375,21 @@ class Oracle:
             for l, (c, f, n) in enumerate(R[b]):
                 B[l, c] = f + n
             D.append(B)
-        A = np.zeros((N * M, N * M))
+        A = np.zeros((N * P * M, N * P * M))
         for kb in range(N):
             for ib in range(N):
-                b = self.block_source(kb, ib)
-                if b is not None:
-                    A[kb * M:(kb + 1) * M, ib * M:(ib + 1) * M] = D[b]
+                for m2 in range(P):
+                    for m1 in range(P):
+                        b = self.block_source(kb, ib, m2, m1)
+                        if b is not None:
+                            r0, c0 = (kb * P + m2) * M, (ib * P + m1) * M
+                            A[r0:r0 + M, c0:c0 + M] = D[b]
         return A
 
     def solve_dense(self, g):
-        """alpha with A alpha = g by dense LU (numpy), shapes (N, M)."""
+        """alpha with A alpha = g by dense LU (numpy), shapes (L, M)."""
         A = self.full_matrix()
-        return np.linalg.solve(A, np.asarray(g, dtype=np.float64).ravel()).reshape(self.N, self.M)
+        return np.linalg.solve(A, np.asarray(g, dtype=np.float64).ravel()).reshape(self.L, self.M)
 
     def dense_block(self, blk):
         """The whole block as a dense M x M array (far + near), row = test vertex."""

@@ -44,6 +44,26 @@ def test_matvec_equals_dense_product():
     assert np.linalg.norm(y - z) <= 1e-13 * np.linalg.norm(z)
 
 
+def test_p1_reduced_matvec_and_dense_product():
+    # p = 1: Eq. relationAtildeBlock holds for every pair of orders (m2, m1),
+    # rows / columns k (p + 1) + m (Sec. 3 numbering); the product loop
+    # against the dense matrix of the directly assembled blocks
+    V, F = inputs.icosphere(0)
+    t = inputs.equidistant_grid(8, 2.1)
+    o = Oracle(V, F, t, p=1)
+    full = Oracle(V, F, t, p=1, equidistant=False)
+    x = _x(o.L, o.M, seed=11)
+    y = o.hessenberg_apply(x)
+    z = full.hessenberg_apply(x)
+    d = (full.full_matrix() @ x.ravel()).reshape(full.L, full.M)
+    assert y.shape == (16, 12) and np.linalg.norm(z) > 0
+    assert np.linalg.norm(y - z) <= 1e-12 * np.linalg.norm(z)
+    assert np.linalg.norm(z - d) <= 1e-13 * np.linalg.norm(d)
+    # orders are not interchangeable: swapping m of x changes y
+    xs = x.reshape(8, 2, 12)[:, ::-1].reshape(16, 12)
+    assert not np.allclose(o.hessenberg_apply(xs), y)
+
+
 def test_diam_cut_is_active_on_long_grid():
     o, full = _pair(17, 6.4)
     lags = {b[0] - b[1] for b in full.blocks()}

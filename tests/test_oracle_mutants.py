@@ -79,14 +79,21 @@ PY_MUTANTS = {
                                       [MV + "::test_reduced_matvec_equals_full_block_matrix"]),
     "superdiagonal from the diagonal block": ("oracle.py", "key = (1, 2)", "key = (1, 1)",
                                               [MV + "::test_reduced_matvec_equals_full_block_matrix"]),
-    "matvec reads x of the test index": ("oracle.py", "np.dot(f + n, x[ib, c])", "np.dot(f + n, x[kb, c])",
+    "matvec reads x of the test index": ("oracle.py", "np.dot(f + n, x[ib * P + m1, c])",
+                                         "np.dot(f + n, x[kb * P + m1, c])",
                                          [MV + "::test_matvec_equals_dense_product"]),
-    "right-hand side tested with b for bdot": ("oracle.py", "bd = self.basis(k, 0, s_n)[:, 1]",
-                                               "bd = self.basis(k, 0, s_n)[:, 0]",
+    "matvec reads x of the test order": ("oracle.py", "np.dot(f + n, x[ib * P + m1, c])",
+                                         "np.dot(f + n, x[ib * P + m2, c])",
+                                         [MV + "::test_p1_reduced_matvec_and_dense_product"]),
+    "right-hand side tested with b for bdot": ("oracle.py", "bd = self.basis(k, m, s_n)[:, 1]",
+                                               "bd = self.basis(k, m, s_n)[:, 0]",
                                                [RHS + "::test_rhs_sphere_n0_closed_form"]),
     "right-hand side weights against reversed points": ("oracle.py", "w7[None, :, None] * bary[None, :, :]",
                                                         "w7[None, :, None] * bary[None, ::-1, :]",
                                                         [RHS + "::test_rhs_plane_wave_brute_force"]),
+    "right-hand side ignores the order m": ("oracle.py", "bd = self.basis(k, m, s_n)[:, 1]",
+                                            "bd = self.basis(k, 0, s_n)[:, 1]",
+                                            ["tests/test_oracle_radial.py::test_mesh_solution_matches_reduction_p1"]),
     "Gram-Schmidt sign": ("krylov.py", "w = w - H[i, j] * V[i]", "w = w + H[i, j] * V[i]",
                           [KR + "::test_gmres_iterate_is_krylov_minimal_residual"]),
     "flexible update with V for Z": ("krylov.py", "x = x + Z[:jdone].T @ y", "x = x + V[:jdone].T @ y",
