@@ -398,3 +398,51 @@ class Oracle:
         for l, (c, f, n) in enumerate(res):
             A[l, c] = f + n
         return A
+
+    def double_layer(self, alpha, X, times, n=8):
+        """Retarded double layer potential u = D phi (Eq. RetardedPotential)
+        of the density phi(y, s) = sum_{k,m,j} alpha[k (p + 1) + m, j]
+        b_{k,m}(s) phi_j(y) at points X (P, 3) off the surface and times
+        `times`:
+
+            u(x, t) = -1/(4 pi) int_Gamma n_y.(x - y)/|x - y|
+                      [phi(y, t - |x - y|)/|x - y|^2
+                       + d_t phi(y, t - |x - y|)/|x - y|] dGamma_y,
+
+        integrated over every flat triangle by a collapsed Gauss product rule
+        with n points per direction ((u, v) -> barycentric (1 - u, u (1 - v),
+        u v), weight 2 u w_u w_v |T|). Returns an array (P, len(times))."""
+        alpha = np.asarray(alpha, dtype=np.float64)
+        P1 = self.p + 1
+        assert alpha.shape == (self.N * P1, self.M)
+        X = np.atleast_2d(np.asarray(X, dtype=np.float64))
+        times = np.atleast_1d(np.asarray(times, dtype=np.float64))
+        g, w = gauss_legendre(n)
+        uu, vv = np.meshgrid(g, g, indexing="ij")
+        lam = np.stack([1.0 - uu, uu * (1.0 - vv), uu * vv], axis=-1).reshape(-1, 3)   # (Q, 3)
+        wq = (2.0 * uu * w[:, None] * w[None, :]).ravel()                               # (Q,)
+        Pt = self.V[self.F]                                                             # (E, 3, 3)
+        cr = np.cross(Pt[:, 1] - Pt[:, 0], Pt[:, 2] - Pt[:, 0])
+        area = 0.5 * np.linalg.norm(cr, axis=1)
+        nrm = cr / (2.0 * area[:, None])
+        Y = np.einsum("qa,ead->eqd", lam, Pt)                                           # (E, Q, 3)
+        W = area[:, None] * wq[None, :]                                                 # (E, Q)
+        coef = np.einsum("qa,lea->leq", lam, alpha[:, self.F])                          # (L, E, Q)
+        out = np.zeros((X.shape[0], times.size))
+        for ip, x in enumerate(X):
+            d = x[None, None, :] - Y
+            r = np.sqrt(np.einsum("eqd,eqd->eq", d, d))
+            kern = np.einsum("ed,eqd->eq", nrm, d) / r * W                              # n_y.(x-y)/r dGamma
+            for it, t in enumerate(times):
+                s = (t - r).ravel()
+                phi = np.zeros(s.size)
+                dphi = np.zeros(s.size)
+                for k in range(self.N):
+                    for m in range(P1):
+                        b = self.basis(k, m, s)
+                        c = coef[k * P1 + m].ravel()
+                        phi += c * b[:, 0]
+                        dphi += c * b[:, 1]
+                integrand = kern.ravel() * (phi / r.ravel() ** 2 + dphi / r.ravel())
+                out[ip, it] = -np.sum(integrand) / (4.0 * np.pi)
+        return out

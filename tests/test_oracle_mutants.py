@@ -19,6 +19,7 @@ from oracle import oracle as O
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 T, S = "tests/test_oracle_time.py", "tests/test_oracle_space.py"
 MV, RHS, KR = "tests/test_oracle_matvec.py", "tests/test_oracle_rhs.py", "tests/test_oracle_krylov.py"
+POT = "tests/test_oracle_potential.py"
 
 # name: (exact source text, planted replacement, pin tests that must fail), in tdbem_oracle.c
 MUTANTS = {
@@ -94,6 +95,13 @@ PY_MUTANTS = {
     "right-hand side ignores the order m": ("oracle.py", "bd = self.basis(k, m, s_n)[:, 1]",
                                             "bd = self.basis(k, 0, s_n)[:, 1]",
                                             ["tests/test_oracle_radial.py::test_mesh_solution_matches_reduction_p1"]),
+    "potential without the d_t phi term": ("oracle.py", "(phi / r.ravel() ** 2 + dphi / r.ravel())",
+                                           "(phi / r.ravel() ** 2)",
+                                           [POT + "::test_sphere_constant_density_reduction"]),
+    "potential sign": ("oracle.py", "out[ip, it] = -np.sum(integrand) / (4.0 * np.pi)",
+                       "out[ip, it] = np.sum(integrand) / (4.0 * np.pi)", [POT + "::test_gauss_law_and_causality"]),
+    "advanced instead of retarded time": ("oracle.py", "s = (t - r).ravel()", "s = (t + r).ravel()",
+                                          [POT + "::test_gauss_law_and_causality"]),
     "Gram-Schmidt sign": ("krylov.py", "w = w - H[i, j] * V[i]", "w = w + H[i, j] * V[i]",
                           [KR + "::test_gmres_iterate_is_krylov_minimal_residual"]),
     "flexible update with V for Z": ("krylov.py", "x = x + Z[:jdone].T @ y", "x = x + V[:jdone].T @ y",
