@@ -1,6 +1,7 @@
 """FP64 CPU oracle of the iterative solution of the block-Hessenberg system
-A alpha = g (Sec. 4): restarted flexible GMRES and the recursive algebraic
-block-Hessenberg preconditioner (Sec. 4.2, Algorithm 1).
+A alpha = g (Sec. 4): restarted flexible GMRES, the recursive algebraic
+block-Hessenberg preconditioner (Sec. 4.2, Algorithm 1) and restarted GMRES
+preconditioned by deflation, DGMRES(m, l) (Sec. 4.1).
 
 TEST INFRASTRUCTURE: only the test suite, `__graft_entry__.smoke()` and the
 CPU-baseline leg of `bench.py` import this module. It never imports the CUDA
@@ -143,3 +144,98 @@ def solve(A, nblk, bs, b, m, tol, max_iter, inner=()):
         P = RecursivePreconditioner(A, nblk, bs, inner, tol)
         prec = P.apply
     return fgmres(lambda v: A @ v, b, m, tol, max_iter, prec)
+
+
+def deflation_inverse(apply_A, U, lam_max):
+    """M^-1 of the deflation preconditioner (Sec. 4.1) for an orthonormal
+    basis U (n, r) of an approximately invariant subspace:
+    M^-1 = I + U (|lam_max| T^-1 - I_r) U^T with T = U^T A U. Returns a
+    function v -> M^-1 v (and T)."""
+    U = np.asarray(U, dtype=np.float64)
+    if U.shape[1] == 0:
+        return (lambda v: np.array(v, dtype=np.float64)), np.zeros((0, 0))
+    AU = np.column_stack([apply_A(U[:, j]) for j in range(U.shape[1])])
+    T = U.T @ AU
+    Tinv = np.linalg.inv(T)
+    lam = abs(float(lam_max))
+
+    def apply(v):
+        v = np.asarray(v, dtype=np.float64)
+        c = U.T @ v
+        return v + U @ (lam * (Tinv @ c) - c)
+    return apply, T
+
+
+def dgmres(apply_A, b, m, l, r, tol, max_iter):
+    """DGMRES(m, l) of Sec. 4.1 for A x = b from x0 = 0: restarted GMRES(m)
+    right-preconditioned by the deflation preconditioner M^-1 of
+    `deflation_inverse`, fixed within a cycle. After every cycle the
+    Schur decomposition H_m = S R S^T of the cycle's square Hessenberg
+    matrix (of A M^-1) is sorted so that its eigenvalues of smallest modulus
+    come first; the first l Schur vectors (l + 1 when the l-th closes a
+    complex pair) give V_m S_l, which is orthonormalised against U (two
+    Gram-Schmidt passes) and appended, until U has r columns. The largest
+    modulus among the eigenvalues of H_m estimates |lambda_max|. l = 0 (or
+    r = 0) is plain GMRES(m).
+
+    Returns (x, iterations, history, U) with history as in fgmres."""
+    import scipy.linalg as sla
+    b = np.asarray(b, dtype=np.float64).ravel()
+    n = b.size
+    x = np.zeros(n)
+    bn = float(np.linalg.norm(b))
+    if bn == 0.0:
+        return x, 0, [0.0], np.zeros((n, 0))
+    U = np.zeros((n, 0))
+    lam_max = 1.0
+    prec = lambda v: np.array(v, dtype=np.float64)
+    total, hist = 0, []
+    while True:
+        res = b - apply_A(x)
+        beta = float(np.linalg.norm(res))
+        hist.append(beta / bn)
+        if beta <= tol * bn or total >= max_iter:
+            return x, total, hist, U
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        V[0] = res / beta
+        y = np.zeros(0)
+        jdone, stop = 0, False
+        for j in range(m):
+            w = apply_A(prec(V[j]))
+            for i in range(j + 1):
+                H[i, j] = np.dot(w, V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            rhs = np.zeros(j + 2)
+            rhs[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], rhs, rcond=None)[0]
+            est = float(np.linalg.norm(rhs - H[:j + 2, :j + 1] @ y))
+            total += 1
+            jdone = j + 1
+            hist.append(est / bn)
+            if est <= tol * bn or total >= max_iter or H[j + 1, j] == 0.0:
+                stop = True
+                break
+        x = x + prec(V[:jdone].T @ y)
+        if stop:
+            return x, total, hist, U
+        if l > 0 and U.shape[1] < r:
+            Hm = H[:m, :m]
+            ev = np.linalg.eigvals(Hm)
+            lam_max = float(np.abs(ev).max())
+            cut = np.sort(np.abs(ev))[min(l, m) - 1]
+            R_, S, sdim = sla.schur(Hm, output="real", sort=lambda re, im: np.hypot(re, im) <= cut * (1 + 1e-12))
+            W = V[:m].T @ S[:, :sdim]
+            for k in range(W.shape[1]):
+                if U.shape[1] >= r:
+                    break
+                u = W[:, k]
+                for _ in range(2):
+                    u = u - U @ (U.T @ u)
+                nu = np.linalg.norm(u)
+                if nu > 1e-10 * np.linalg.norm(W[:, k]):
+                    U = np.column_stack([U, u / nu])
+            prec, _ = deflation_inverse(apply_A, U, lam_max)

@@ -12,11 +12,16 @@ recursive block-Hessenberg preconditioner of Sec. 4.2 (Algorithm 1).
 * Woodbury structure (Sec. 4.2): A M^-1 - I has rank at most one block.
 * The restarted solve reaches the dense solution of the assembled
   space-time system, preconditioned or not.
+* Deflation (Sec. 4.1): M^-1 = I + U (|lam| T^-1 - I) U^T inverts
+  M = I + U (T/|lam| - I) U^T, and with U an exact invariant subspace of the
+  r smallest eigenvalues the spectrum of A M^-1 is lam_{r+1}, ..., lam_n
+  and |lam_n| (r times); DGMRES(m, 0) is GMRES(m), and DGMRES(m, l)
+  converges where GMRES(m) stalls.
 """
 import numpy as np
 import pytest
 
-from oracle.krylov import RecursivePreconditioner, fgmres, solve
+from oracle.krylov import RecursivePreconditioner, deflation_inverse, dgmres, fgmres, solve
 
 
 def _rand_hessenberg(nblk, bs, seed, shift=4.0):
@@ -142,3 +147,48 @@ def test_solve_reaches_dense_solution(system, inner):
     assert hist[-1] <= 1e-10
     assert np.linalg.norm(A @ x - g) <= 1.5e-10 * np.linalg.norm(g)
     assert np.linalg.norm(x - ref) <= 1e-6 * np.linalg.norm(ref), (inner, it)
+
+
+def _small_eigen_matrix(n=80, seed=0):
+    """Q R Q^T with Q orthogonal, R upper triangular: eigenvalues the
+    diagonal, four of modulus <= 0.05 and the rest in [1, 10]."""
+    rng = np.random.default_rng(seed)
+    Q = np.linalg.qr(rng.standard_normal((n, n)))[0]
+    d = np.concatenate([[1e-2, 2e-2, -3e-2, 5e-2], rng.uniform(1.0, 10.0, n - 4)])
+    R = np.diag(d) + np.triu(rng.standard_normal((n, n)) * 0.05, 1)
+    return Q @ R @ Q.T, d
+
+
+def test_deflation_preconditioner_claims():
+    import scipy.linalg as sla
+    A, d = _small_eigen_matrix()
+    n = A.shape[0]
+    _, S, r = sla.schur(A, output="real", sort=lambda re, im: np.hypot(re, im) < 0.1)
+    assert r == 4
+    U = S[:, :r]
+    lam = np.abs(d).max()
+    Minv, T = deflation_inverse(lambda v: A @ v, U, lam)
+    Mi = np.column_stack([Minv(e) for e in np.eye(n)])
+    M = np.eye(n) + U @ (T / lam - np.eye(r)) @ U.T
+    assert np.abs(M @ Mi - np.eye(n)).max() < 1e-11
+    ev = np.sort_complex(np.linalg.eigvals(A @ Mi))
+    want = np.sort_complex(np.concatenate([d[4:], [lam] * r]).astype(complex))
+    assert np.abs(ev - want).max() < 1e-5
+
+
+def test_dgmres_without_deflation_is_gmres():
+    A, _ = _small_eigen_matrix(seed=2)
+    b = np.random.default_rng(3).standard_normal(A.shape[0])
+    x1, it1, h1 = fgmres(lambda v: A @ v, b, 10, 1e-10, 120)
+    x2, it2, h2, U = dgmres(lambda v: A @ v, b, 10, 0, 8, 1e-10, 120)
+    assert it1 == it2 and np.array_equal(x1, x2) and U.shape[1] == 0
+
+
+def test_dgmres_restores_convergence():
+    A, _ = _small_eigen_matrix()
+    b = np.random.default_rng(1).standard_normal(A.shape[0])
+    x0, it0, _ = fgmres(lambda v: A @ v, b, 10, 1e-10, 600)
+    assert np.linalg.norm(b - A @ x0) > 1e-2 * np.linalg.norm(b)  # GMRES(10) stalls
+    x, it, _, U = dgmres(lambda v: A @ v, b, 10, 2, 8, 1e-10, 600)
+    assert it < 200 and U.shape[1] == 8
+    assert np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)

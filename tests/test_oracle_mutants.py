@@ -102,6 +102,11 @@ PY_MUTANTS = {
                        "out[ip, it] = np.sum(integrand) / (4.0 * np.pi)", [POT + "::test_gauss_law_and_causality"]),
     "advanced instead of retarded time": ("oracle.py", "s = (t - r).ravel()", "s = (t + r).ravel()",
                                           [POT + "::test_gauss_law_and_causality"]),
+    "deflation inverse sign": ("krylov.py", "return v + U @ (lam * (Tinv @ c) - c)", "return v + U @ (lam * (Tinv @ c) + c)",
+                               [KR + "::test_deflation_preconditioner_claims"]),
+    "deflation keeps the largest Ritz values": ("krylov.py", "cut = np.sort(np.abs(ev))[min(l, m) - 1]",
+                                                "cut = np.sort(np.abs(ev))[::-1][min(l, m) - 1]",
+                                                [KR + "::test_dgmres_restores_convergence"]),
     "Gram-Schmidt sign": ("krylov.py", "w = w - H[i, j] * V[i]", "w = w + H[i, j] * V[i]",
                           [KR + "::test_gmres_iterate_is_krylov_minimal_residual"]),
     "flexible update with V for Z": ("krylov.py", "x = x + Z[:jdone].T @ y", "x = x + V[:jdone].T @ y",
