@@ -74,7 +74,7 @@ MUTANTS = {
 }
 
 
-# the same for the Python parts: (file in oracle/, text, replacement, pins)
+# the same for the Python parts: (file in oracle/, text or (anchor, text), replacement, pins)
 PY_MUTANTS = {
     "reused block of the wrong lag": ("oracle.py", "key = (d + 1, 1)", "key = (d, 1)",
                                       [MV + "::test_reduced_matvec_equals_full_block_matrix"]),
@@ -107,7 +107,7 @@ PY_MUTANTS = {
     "deflation keeps the largest Ritz values": ("krylov.py", "cut = np.sort(np.abs(ev))[min(l, m) - 1]",
                                                 "cut = np.sort(np.abs(ev))[::-1][min(l, m) - 1]",
                                                 [KR + "::test_dgmres_restores_convergence"]),
-    "Gram-Schmidt sign": ("krylov.py", "w = w - H[i, j] * V[i]", "w = w + H[i, j] * V[i]",
+    "Gram-Schmidt sign": ("krylov.py", ("def fgmres(", "w = w - H[i, j] * V[i]"), "w = w + H[i, j] * V[i]",
                           [KR + "::test_gmres_iterate_is_krylov_minimal_residual"]),
     "flexible update with V for Z": ("krylov.py", "x = x + Z[:jdone].T @ y", "x = x + V[:jdone].T @ y",
                                      [KR + "::test_fixed_preconditioner_is_right_preconditioned_gmres"]),
@@ -147,9 +147,16 @@ def _run_py(name, tmp, lib):
         shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(pkg, "oracle", f))
     target = os.path.join(pkg, "oracle", fname)
     src = open(target).read()
-    assert src.count(old) == 1, "%s: the planted text must occur once in oracle/%s" % (name, fname)
+    start = 0
+    if isinstance(old, tuple):  # (anchor, text): the first occurrence of text after the anchor
+        anchor, old = old
+        assert src.count(anchor) == 1, "%s: the anchor must occur once in oracle/%s" % (name, fname)
+        start = src.index(anchor)
+    else:
+        assert src.count(old) == 1, "%s: the planted text must occur once in oracle/%s" % (name, fname)
+    at = src.index(old, start)
     with open(target, "w") as f:
-        f.write(src.replace(old, new))
+        f.write(src[:at] + new + src[at + len(old):])
     # the copy comes first on the path (cwd); the repository follows for the rest
     env = dict(os.environ, TDBEM_ORACLE_LIB=lib, PYTHONPATH=os.pathsep.join([pkg, ROOT]))
     return _pins([os.path.join(ROOT, n) for n in nodes], env, pkg)
