@@ -37,6 +37,7 @@ CONFIGS = {
     "sphere20480": "icosphere 20480 triangles / 10242 vertices, N=129 points, dt=0.05 on [0,6.4], c=1, p=0",
     "sphere5120j": "icosphere 5120 / 2562 jittered +-1% h (seed 0), N=65 points, dt=0.0625 on [0,4], c=1, p=0",
     "sphere320": "icosphere 320 / 162, N=17 points, dt=0.25 on [0,4], c=1, p=0",
+    "sphere5120p": "icosphere 5120 / 2562, N=65 points, dt=0.07 on [0,4.48], c=1, p=0 (far-kernel profiling case)",
     "torus8192g": "torus R=1 r=0.4, 128x32 quads (8192 triangles / 4096 vertices), graded grid of 96 steps "
                   "with ratio 1.02 on [0,6] (N=97 points), c=1, p=0; every nonzero block assembled",
     "torus2048g": "torus R=1 r=0.4, 64x16 quads (2048 triangles / 1024 vertices), the same graded grid",

@@ -390,6 +390,7 @@ struct tdbem_asm {
     std::vector<int64_t> color_off;
     int ss_npp[4] = {0, 0, 0, 0};
     ChebF32 c32{};
+    ChebLag32 c32s{};  // lag-class panels for the mixed far kernel (term-major, signed)
     std::vector<int64_t> nnz_far, nnz_near, off_far, off_near;
     bool assembled = false;
     tdbem_stats_t stats{};
@@ -798,8 +799,12 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     A->OFF = (int)ceil(spread + 1e-9);
     if (A->OFF < 1) A->OFF = 1;
     if (A->OFF > 3) return bail(fail(TDBEM_E_UNSUPPORTED, "triangles too large for the time step (2 max|x - c|/dt > 3)"));
+    if (!A->fp64 && far32_window(mesh->max_dq, dt) > 5)
+        return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: triangles too large for the time step"));
     A->KW = 4 + (int)ceil(2.0 * mesh->max_star / dt) + 2;
     if (A->KW > 16) return bail(fail(TDBEM_E_UNSUPPORTED, "vertex stars too large for the time step (lag window > 16)"));
+    if (!A->fp64 && far32_smem(far32_window(mesh->max_dq, dt), A->KW, mesh->max_nv) > 227 * 1024)
+        return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: far-kernel shared memory exceeds 227 KB"));
     const tdbem_mesh &m = *mesh;
     // uploads
     std::vector<int32_t> colors;
@@ -813,6 +818,15 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     UP(adj_perm, m.adj_perm); UP(adj_nbr, m.adj_nbr); UP(nbr_ptr, m.nbr_ptr); UP(nbr, m.nbr);
     UP(chunk_vptr, m.chunk_vptr); UP(chunk_vert, m.chunk_vert); UP(chunk_sptr, m.chunk_sptr);
     UP(chunk_src, m.chunk_src); UP(colors, colors); UP(rule_w, rw); UP(rule_l, rl); UP(tgrid, tg->t);
+    {
+        std::vector<float> geol(16 * m.E), cenh(3 * m.E), cenl(3 * m.E);
+        for (int64_t k = 0; k < 16 * m.E; ++k) geol[k] = (float)(m.geo64[k] - (double)m.geo32[k]);
+        for (int64_t k = 0; k < 3 * m.E; ++k) {
+            cenh[k] = (float)m.cen[k];
+            cenl[k] = (float)(m.cen[k] - (double)cenh[k]);
+        }
+        UP(g_geol, geol); UP(g_cenh, cenh); UP(g_cenl, cenl);
+    }
     std::vector<double> rw64(7), rl64(21);
     for (int k = 0; k < 7; ++k) { rw64[k] = m.rule_W[k]; for (int d = 0; d < 3; ++d) rl64[3 * k + d] = m.rule_L[k][d]; }
     UP(rule_w64, rw64); UP(rule_l64, rl64);
@@ -1042,6 +1056,11 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                     const double v = c1[((size_t)p * NCHEB + n) * 2 + k];
                     A->c32.c[p][n][k] = (float)v;
                     if (n < NCHEB_LO) A->c32.lo[p][n][k] = (float)(v - (double)(float)v);
+                    const float sg = (n & 2) ? -1.f : 1.f;
+                    if (p < TOTAL_LAG_PANELS) {
+                        A->c32s.c[n][p][k] = sg * A->c32.c[p][n][k];
+                        if (n < NCHEB_LO) A->c32s.lo[n][p][k] = sg * A->c32.lo[p][n][k];
+                    }
                 }
     }
     // ---- element-pair bounds, vertex-pair windows
@@ -1075,10 +1094,23 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
         fa.dense = (double *)A->dense.p; fa.dense_spec = (double *)A->dense_spec.p; fa.KW = A->KW;
         fa.status = (int *)A->status.p;
         fa.cheb64 = (const double *)A->tab_coef4.p;
+        fa.cenh = (const float *)A->g_cenh.p; fa.cenl = (const float *)A->g_cenl.p;
+        fa.geoh = (const float *)A->geo32.p; fa.geol = (const float *)A->g_geol.p;
         for (int k = 0; k < 7; ++k) {
             fa.rw32[k] = (float)m.rule_W[k];
             fa.wwh[k] = (float)m.rule_W[k];
             fa.wwl[k] = (float)(m.rule_W[k] - (double)fa.wwh[k]);
+            if (k == 0 || k == 1 || k == 4) {
+                const int o = k == 0 ? 0 : (k == 1 ? 1 : 2);
+                // a = corner 1 of point k (0 on orbits 1, 2; any at the centroid) is a non-distinguished corner
+                const double kk = m.rule_W[k] * m.rule_L[k][k == 0 ? 0 : 1];
+                fa.okh[o] = (float)kk; fa.okl[o] = (float)(kk - (double)fa.okh[o]);
+                fa.owh[o] = (float)m.rule_W[k]; fa.owl[o] = (float)(m.rule_W[k] - (double)fa.owh[o]);
+                if (o > 0) {
+                    const double dd = m.rule_W[k] * (m.rule_L[k][0] - m.rule_L[k][1]);
+                    fa.odh[o - 1] = (float)dd; fa.odl[o - 1] = (float)(dd - (double)fa.odh[o - 1]);
+                }
+            }
             for (int d = 0; d < 3; ++d) {
                 fa.rl32[3 * k + d] = (float)m.rule_L[k][d];
                 const double gw = m.rule_W[k] * m.rule_L[k][d];
@@ -1086,10 +1118,10 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                 fa.gwl[3 * k + d] = (float)(gw - (double)fa.gwh[3 * k + d]);
             }
         }
-        const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)nsm);
+        const int grid = (int)std::min<int64_t>(fa.ncolor, (int64_t)(A->fp64 ? 1 : 2) * nsm);
         if (grid > 0) {
             if (A->fp64) launch_far(fa, A->c32, true, A->OFF, A->S64, grid, st);
-            else launch_far32(fa, A->c32, A->OFF, grid, st);
+            else launch_far32(fa, A->c32s, far32_window(m.max_dq, A->tg->dt), grid, st);
         }
     }
     CUDA_TRY(cudaGetLastError());

@@ -39,6 +39,7 @@ constexpr int NSPEC = 5;  // the rest carry lag 0 only
 constexpr int NCHEB = 33; // Chebyshev coefficients per panel (degree 32)
 constexpr int MAXPANEL = 4;
 constexpr int TOTAL_PANELS = 3 + 4 + 3 + 1 + 1 + 2 + 1 + 1;  // sum of P_c = 16
+constexpr int TOTAL_LAG_PANELS = 3 + 4 + 3;                   // panels of C1..C3
 
 struct ClassDesc {
     int rho;      // first panel starts at q - d = rho
@@ -101,6 +102,15 @@ struct alignas(8) ChebF32 {  // 8-aligned: read as packed pairs
     float lo[TOTAL_PANELS][NCHEB_LO][2];  // c - (double)(float)c of the leading ones
 };
 
+// The lag-class panels (C1: 0-2, C2: 3-6, C3: 7-9) for the mixed far kernel,
+// term-major (the 10 coefficient pairs of one term are adjacent in the
+// constant bank), with the sign pattern of its Chebyshev recurrence folded
+// in: s_n c_n, s_n = +1, +1, -1, -1, ... by n mod 4.
+struct alignas(8) ChebLag32 {
+    float c[NCHEB][TOTAL_LAG_PANELS][2];
+    float lo[NCHEB_LO][TOTAL_LAG_PANELS][2];
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
 // table.cu
 void launch_psi_samples(const double *t, int N, const int *panel_class, const int *panel_kb,
@@ -156,16 +166,26 @@ struct FarArgs {
     int max_nv;                // most trial vertices in one chunk
     float gwh[21], gwl[21];    // w_k lambda_a(p_k) as FP32 pairs (hi, lo), index 3k + a
     float wwh[7], wwl[7];      // w_k as FP32 pairs
+    // the 7-point rule by its orbits (centroid; points 1+k and 4+k with the
+    // distinguished barycentric at corner k), FP32 pairs: w_0 / 3, w_1 a_1,
+    // w_2 a_2 (kh, kl); w_0, w_1, w_2 (wh, wl); w_1 (b_1 - a_1), w_2 (b_2 - a_2)
+    // (dh, dl), so that w_x lambda_a(x) = k_o + [a = k] d_o on orbit o
+    float okh[3], okl[3], owh[3], owl[3], odh[2], odl[2];
     double *dense;             // 3 x M x M x KW lag windows, FP64 accumulation
     double *dense_spec;        // 5 x M x M
     int KW;
     int *status;
     const double *cheb64;      // TOTAL_PANELS * S * NCHEB * 2 (FP64 path)
+    const float *cenh, *cenl;  // E x 3 centroids as FP32 pairs (mixed path)
+    const float *geoh, *geol;  // E x 16 geometry (n, area, curls) as FP32 pairs
 };
 void launch_far(const FarArgs &a, const ChebF32 &c32, bool fp64, int off, int S, int grid,
                 cudaStream_t st);
-// far32.cu
-void launch_far32(const FarArgs &a, const ChebF32 &c32, int off, int grid, cudaStream_t st);
+// far32.cu: W is the thread window in unit cells of r / dt,
+// far32_window(max |y - c|, dt)
+int far32_window(double max_dq, double dt);
+size_t far32_smem(int W, int KW, int max_nv);
+void launch_far32(const FarArgs &a, const ChebLag32 &c32, int W, int grid, cudaStream_t st);
 
 // near.cu
 struct NearArgs {

@@ -183,6 +183,10 @@ def workload(name: str) -> Workload:
     torus2048g  : the same torus and grid on 64x16 quads (2048 / 1024), a
                   small case of the same kernels (profiling, parity)
     sphere20480 : icosphere level 5 (20480 / 10242), N=129, dt=0.05, T=6.4
+    sphere5120p : icosphere level 4 (5120 / 2562), N=65, dt=0.07, T=4.48: a
+                  small case of the 20480 sphere's far-kernel shape (the 7
+                  points of a triangle span less than one time step, as
+                  there), for profiling
     """
     if name == "sphere320":
         V, F = icosphere(2)
@@ -199,6 +203,9 @@ def workload(name: str) -> Workload:
     if name == "sphere20480":
         V, F = icosphere(5)
         return Workload(name, V, F, equidistant_grid(129, 6.4), True)
+    if name == "sphere5120p":
+        V, F = icosphere(4)
+        return Workload(name, V, F, equidistant_grid(65, 4.48), True)
     raise KeyError(name)
 
 
