@@ -382,7 +382,7 @@ struct tdbem_asm {
     std::vector<std::vector<double>> lag_a, lag_b;
     // device buffers
     DevBuf F, V, cen, dq, dq32, geo32, geo64, vt_ptr, vt_tri, adj_ptr, adj_tri, adj_perm, adj_nbr,
-        nbr_ptr, nbr, chunk_vptr, chunk_vert, chunk_sptr, chunk_src, colors, rule_w, rule_l, tgrid,
+        nbr_ptr, nbr, chunk_vptr, chunk_vert, chunk_sptr, chunk_src, chunk_hdr, colors, rule_w, rule_l, tgrid,
         rule_w64, rule_l64, lagA, lagB, rec, wdlo, wdhi, wsmask, dense, dense_spec, ndense, ndense_spec, status,
         cls_dlo_d, cls_dhi_d, blk_of_lag_d, lag_base_d, blk_of_spec_d, cnt_far, cnt_near, rp_far,
         rp_near, tot_far, tot_near, off_far_d, off_near_d, col_far, val_far, col_near, val_near,
@@ -803,6 +803,8 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
         return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: triangles too large for the time step"));
     A->KW = 4 + (int)ceil(2.0 * mesh->max_star / dt) + 2;
     if (A->KW > 16) return bail(fail(TDBEM_E_UNSUPPORTED, "vertex stars too large for the time step (lag window > 16)"));
+    if (!A->fp64 && 3.0 * (double)mesh->M * (double)mesh->M >= 2147483647.0)
+        return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: 3 M^2 lag-window rows exceed the int32 row index"));
     if (!A->fp64 && far32_smem(far32_window(mesh->max_dq, dt), A->KW, mesh->max_nv) > 227 * 1024)
         return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: far-kernel shared memory exceeds 227 KB"));
     const tdbem_mesh &m = *mesh;
@@ -817,6 +819,15 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     UP(vt_ptr, m.vt_ptr); UP(vt_tri, m.vt_tri); UP(adj_ptr, m.adj_ptr); UP(adj_tri, m.adj_tri);
     UP(adj_perm, m.adj_perm); UP(adj_nbr, m.adj_nbr); UP(nbr_ptr, m.nbr_ptr); UP(nbr, m.nbr);
     UP(chunk_vptr, m.chunk_vptr); UP(chunk_vert, m.chunk_vert); UP(chunk_sptr, m.chunk_sptr);
+    {
+        std::vector<int32_t> hdr(4 * m.nchunks);
+        for (int64_t ch = 0; ch < m.nchunks; ++ch) {
+            const int32_t v0 = m.chunk_vptr[ch], v1 = m.chunk_vptr[ch + 1];
+            hdr[4 * ch] = v0; hdr[4 * ch + 1] = v1 - v0;
+            hdr[4 * ch + 2] = m.chunk_sptr[v0]; hdr[4 * ch + 3] = m.chunk_sptr[v1] - m.chunk_sptr[v0];
+        }
+        UP(chunk_hdr, hdr);
+    }
     UP(chunk_src, m.chunk_src); UP(colors, colors); UP(rule_w, rw); UP(rule_l, rl); UP(tgrid, tg->t);
     {
         std::vector<float> geol(16 * m.E), cenh(3 * m.E), cenl(3 * m.E);
@@ -1087,6 +1098,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
         fa.ncolor = A->color_off[c + 1] - A->color_off[c];
         fa.chunk_vptr = (const int32_t *)A->chunk_vptr.p; fa.chunk_vert = (const int32_t *)A->chunk_vert.p;
         fa.chunk_sptr = (const int32_t *)A->chunk_sptr.p; fa.chunk_src = (const int32_t *)A->chunk_src.p;
+        fa.chunk_hdr = (const int4 *)A->chunk_hdr.p;
         fa.nchunks = m.nchunks;
         fa.max_nv = m.max_nv;
         fa.rule_w = (const float *)A->rule_w.p; fa.rule_l = (const float *)A->rule_l.p;

@@ -99,6 +99,30 @@ __device__ __forceinline__ f2 lo2(const ChebLag32 &C, int p, int n) {
     return *reinterpret_cast<const f2 *>(&C.lo[n][p][0]);
 }
 
+// mbarrier helpers: completion of the scatter (P3) of a chunk, awaited
+// before its shared memory is reused. The wait gives up after a bounded
+// number of polls and flags the status word instead of hanging.
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+    unsigned long long st;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(addr) : "memory");
+    (void)st;
+}
+__device__ __forceinline__ void mbar_wait(unsigned addr, unsigned parity, int *status) {
+    for (int i = 0; i < (1 << 22); ++i) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return;
+    }
+    *status = ST_WAIT;
+}
+
 // ---- FP32-pair (double-float) arithmetic of the element-pair setup --------
 // values h + l with |l| <= ulp(h) / 2; error-free transformations with FMA
 struct DF {
@@ -122,17 +146,18 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
 __device__ __forceinline__ DF df_dot3(const DF *a, const DF *b) {
     return df_add(df_add(df_mul(a[0], b[0]), df_mul(a[1], b[1])), df_mul(a[2], b[2]));
 }
-// a / b: quotient of the high parts, one correction from the remainder
-__device__ __forceinline__ DF df_div(DF a, DF b) {
-    const float q = a.h / b.h;
+// a / b with ib an approximation of 1 / b.h: quotient of the high parts, one
+// correction from the exact remainder (the correction absorbs the error of q)
+__device__ __forceinline__ DF df_div(DF a, DF b, float ib) {
+    const float q = a.h * ib;
     const DF r = df_add(a, df_mul(DF{-q, 0.f}, b));
-    return df_fast(q, r.h / b.h);
+    return df_add(DF{q, 0.f}, DF{r.h * ib, 0.f});
 }
 __device__ __forceinline__ DF df_sqrt(DF a) {
-    const float s = sqrtf(a.h);
+    const float s = a.h * rsqrtf(a.h);
     const float p = s * s;
     const float e = fmaf(s, s, -p);
-    return df_fast(s, ((a.h - p) - e + a.l) / (s + s));
+    return df_add(DF{s, 0.f}, DF{((a.h - p) - e + a.l) * (0.5f * rsqrtf(a.h)), 0.f});
 }
 
 // Per-thread window of W unit cells of q: the 7 trial points of sigma lie
@@ -262,7 +287,8 @@ __device__ __forceinline__ void acc_class(f2 *a01, f2 *a2s, const f2 (&v)[TOTAL_
 // s~) and the window start rbase[xw 32 + lane] (cells above floor(R0 / dt)).
 template <int W>
 __device__ __forceinline__ void quad_thread(const FarArgs &A, const ChebLag32 &C, const Setup32 &su, int xw,
-                                            int lane, float dx0, float dx1, float dx2, float4 *red, int *rbase) {
+                                            int lane, float dx0, float dx1, float dx2, float4 *red, int *rbase,
+                                            unsigned mbar, int64_t it) {
     constexpr int NT = Win<W>::NT;
     f2 a01[NT], a2s[NT];
 #pragma unroll
@@ -331,6 +357,8 @@ __device__ __forceinline__ void quad_thread(const FarArgs &A, const ChebLag32 &C
         acc_class<W, C2>(a01, a2s, v, cell, F01, F2W);
         acc_class<W, C3>(a01, a2s, v, cell, F01, F2W);
     }
+    // red shares its space with the previous chunk's P3 values: wait for it
+    if (it > 0) mbar_wait(mbar, (unsigned)((it - 1) & 1), A.status);
 #pragma unroll
     for (int s = 0; s < NT; ++s) {
         float t0, t1, t2, st;
@@ -376,7 +404,8 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
             f0h = f0.h;
             f0l = f0.l;
             R0 = r0.h;
-            for (int k = 0; k < 3; ++k) Dv[k] = df_div(d[k], r0);
+            const float ir = __frcp_rn(r0.h);
+            for (int k = 0; k < 3; ++k) Dv[k] = df_div(d[k], r0, ir);
         }
         // geometric factors: |tau||sigma|/(4 pi) (n.n, curl_a.curl_b)
         const float *gth = A.geoh + 16 * tau, *gtl = A.geol + 16 * tau;
@@ -418,48 +447,54 @@ __device__ __forceinline__ void chunk_setup(const FarArgs &A, int64_t tau, int64
 }
 
 // The chunk's scatter inputs. Plan: vertex list, sources (sigma_local * 3 +
-// corner) per vertex, and the lag-window bounds of every (vertex, test
-// corner, class) item; read-only, so it is fetched one chunk ahead, by all
-// threads during P2. Window values: copied (cp.async) into shared memory by
-// the producer at the start of the chunk's P1, after the previous chunk's
-// P3 has stored its windows; P3 then reads only shared memory.
+// corner) per vertex (fetched by the producer during the previous chunk's
+// P1), and the lag-window bounds of every (vertex, test corner, class) item
+// (fetched by all threads during the previous chunk's P2): read-only inputs,
+// so they are fetched one chunk ahead. Window values: copied (cp.async) into
+// shared memory by the producer at the start of the chunk's P1, after the
+// previous chunk's P3 has stored its windows; P3 then reads only shared
+// memory.
 struct Stage32 {
     int nv, nitems;
     int32_t vert[64];
     int32_t sptr[65];
     int32_t src[96];
 };
-// The plan of chunk ch for test corners (Ft0, Ft1, Ft2), fetched by all
-// threads of the CTA (thread t: items t, t + 256, ...)
-__device__ __forceinline__ void stage_plan(const FarArgs &A, int32_t Ft0, int32_t Ft1, int32_t Ft2, int64_t ch,
-                                           Stage32 &sg, int16_t *swlo, int16_t *swhi) {
+// The plan of chunk ch: vertex list and sources (the same for every test
+// triangle), fetched by one warp (lane = this thread's lane)
+__device__ __forceinline__ void stage_chunk_plan(const FarArgs &A, int64_t ch, int lane, Stage32 &sg) {
+    const int4 h = A.chunk_hdr[ch];  // v0, nv, x0, nsrc
+    for (int v = lane; v < h.y; v += 32) sg.vert[v] = A.chunk_vert[h.x + v];
+    for (int v = lane; v <= h.y; v += 32) sg.sptr[v] = A.chunk_sptr[h.x + v] - h.z;
+    for (int x = lane; x < h.w; x += 32) sg.src[x] = A.chunk_src[h.z + x];
+    if (lane == 0) { sg.nv = h.y; sg.nitems = h.y * 3 * NLAG; }
+}
+// the lag-window bounds and window rows (c M^2 + l M + j, below 2^31) of
+// every item of a staged plan for test corners (Ft0, Ft1, Ft2), fetched by
+// all threads of the CTA
+__device__ __forceinline__ void stage_bounds(const FarArgs &A, int32_t Ft0, int32_t Ft1, int32_t Ft2,
+                                             const Stage32 &sg, int16_t *swlo, int16_t *swhi, int32_t *srow) {
     const int64_t M = A.g.M, MM = M * M;
-    const int t = threadIdx.x;
-    const int v0 = A.chunk_vptr[ch], nv = A.chunk_vptr[ch + 1] - v0;
-    const int x0 = A.chunk_sptr[v0], nsrc = A.chunk_sptr[v0 + nv] - x0;
-    if (t < nv) sg.vert[t] = A.chunk_vert[v0 + t];
-    if (t <= nv) sg.sptr[t] = A.chunk_sptr[v0 + t] - x0;
-    if (t < nsrc) sg.src[t] = A.chunk_src[x0 + t];
-    if (t == 0) { sg.nv = nv; sg.nitems = nv * 3 * NLAG; }
-    const int nitems = nv * 3 * NLAG;
-    for (int it = t; it < nitems; it += F32_THREADS_ALL) {
+    for (int it = threadIdx.x; it < sg.nitems; it += F32_THREADS_ALL) {
         const int v = it / (3 * NLAG), rem = it % (3 * NLAG);
         const int a = rem / NLAG, c = rem % NLAG;
-        const int64_t o = c * MM + (int64_t)(a == 0 ? Ft0 : a == 1 ? Ft1 : Ft2) * M + A.chunk_vert[v0 + v];
+        const int64_t o = c * MM + (int64_t)(a == 0 ? Ft0 : a == 1 ? Ft1 : Ft2) * M + sg.vert[v];
         swlo[it] = A.dlo[o];
         swhi[it] = A.dhi[o];
+        srow[it] = (int32_t)o;
     }
 }
-__device__ __forceinline__ void stage_windows(const FarArgs &A, const Setup32 &su, int lane, const Stage32 &sg,
+// row stride of the staged windows in FP32 pairs: odd, so that lanes reading
+// different rows hit different shared-memory banks
+__device__ __forceinline__ int kw_stride(int KW) { return KW | 1; }
+__device__ __forceinline__ void stage_windows(const FarArgs &A, int lane, const Stage32 &sg, const int32_t *srow,
                                               FF *stg) {
-    const int64_t M = A.g.M, MM = M * M;
-    const int KW = A.KW;
+    const int KW = A.KW, KS = kw_stride(KW);
+    // lane per row: 8-byte copies of its KW words (a mapping of lanes onto
+    // consecutive words of a few rows measured slower)
     for (int it = lane; it < sg.nitems; it += 32) {
-        const int v = it / (3 * NLAG), rem = it % (3 * NLAG);
-        const int a = rem / NLAG, c = rem % NLAG;
-        const int64_t o = c * MM + (int64_t)su.Ft[a] * M + sg.vert[v];
-        const FF *src = reinterpret_cast<const FF *>(A.dense) + o * KW;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(stg + (size_t)it * KW);
+        const FF *src = reinterpret_cast<const FF *>(A.dense) + (int64_t)srow[it] * KW;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(stg + (size_t)it * KS);
         for (int k = 0; k < KW; ++k)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst + 8 * k), "l"(src + k));
     }
@@ -619,9 +654,8 @@ __device__ __forceinline__ void reduce_item(const FarArgs &A, const Setup32 &su,
 // union slot 0 plus rho_c + P_c - 1.
 template <int W>
 __device__ __forceinline__ void scatter_chunk32(const FarArgs &A, const Setup32 &su, const Stage32 &sg, FF *stg,
-                                                const int16_t *swlo, const int16_t *swhi, const FF *Lb,
-                                                const int *ub) {
-    const int64_t M = A.g.M, MM = M * M;
+                                                const int16_t *swlo, const int16_t *swhi, const int32_t *srow,
+                                                const FF *Lb, const int *ub) {
     const int KW = A.KW;
     for (int it = threadIdx.x; it < sg.nitems; it += F32_THREADS_ALL) {
         const int v = it / (3 * NLAG), rem = it % (3 * NLAG);
@@ -632,7 +666,7 @@ __device__ __forceinline__ void scatter_chunk32(const FarArgs &A, const Setup32 
         const int ou = c == C1 ? Win<W>::ou(C1) : c == C2 ? Win<W>::ou(C2) : Win<W>::ou(C3);
         const int rho = A.lt.rho[c];
         const int wlo = swlo[it], whi = min((int)swhi[it], wlo + KW - 1);
-        FF *cur = stg + (size_t)it * KW;
+        FF *cur = stg + (size_t)it * kw_stride(KW);
         int dmn = 1 << 30, dmx = -(1 << 30);
         for (int x = s0; x < s1; ++x) {
             const int src = sg.src[x], sl = src / 3, b = src % 3;
@@ -649,7 +683,7 @@ __device__ __forceinline__ void scatter_chunk32(const FarArgs &A, const Setup32 
                 if (u >= u0 && u <= u1) cw[u] = ff_plus(cw[u], lb[u * 9 * 32]);
         }
         if (dmn > dmx) continue;
-        FF *dst = reinterpret_cast<FF *>(A.dense) + (c * MM + (int64_t)su.Ft[a] * M + sg.vert[v]) * KW;
+        FF *dst = reinterpret_cast<FF *>(A.dense) + (int64_t)srow[it] * KW;
         for (int d = dmn; d <= dmx; ++d) dst[d - wlo] = cur[d - wlo];
     }
 }
@@ -666,12 +700,13 @@ struct Smem32 {
     static constexpr size_t LB = sizeof(FF) * 32 * Win<W>::NU * 9;
     static constexpr size_t RED = RED0 > LB ? RED0 : LB;
     static constexpr size_t STAGE = ((sizeof(Stage32) + 15) / 16) * 16;
-    static constexpr size_t FIXED = SETUP + RED + sizeof(int) * (F32_XW * 32 + 32) + 2 * STAGE;
+    static constexpr size_t FIXED = SETUP + RED + sizeof(int) * (F32_XW * 32 + 32) + 16 + 2 * STAGE;
     // plus the staged windows, (max_nv 9) x KW FP32 pairs, and two sets of
     // int16 bounds (this chunk's and the next one's)
     static size_t bytes(int KW, int max_nv) {
         const size_t items = (size_t)max_nv * 3 * NLAG;
-        return FIXED + items * sizeof(FF) * KW + ((4 * items * sizeof(int16_t) + 15) / 16) * 16;
+        return FIXED + items * sizeof(FF) * (KW | 1) + ((4 * items * sizeof(int16_t) + 15) / 16) * 16 +
+               2 * items * sizeof(int32_t);
     }
 };
 
@@ -691,12 +726,14 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
     p += Smem32<W>::RED;
     int *rbase = reinterpret_cast<int *>(p);             // [7][32]
     int *ub = rbase + F32_XW * 32;                       // [32]
-    p += sizeof(int) * (F32_XW * 32 + 32);
+    unsigned long long *p3bar = reinterpret_cast<unsigned long long *>(ub + 32);  // P3 completion
+    p += sizeof(int) * (F32_XW * 32 + 32) + 16;
     Stage32 *sgs = reinterpret_cast<Stage32 *>(p);       // [2]
     p += 2 * Smem32<W>::STAGE;
     const int nitm = A.max_nv * 3 * NLAG;
-    FF *stg = reinterpret_cast<FF *>(p);                 // [max_nv 9][KW]
-    int16_t *sw = reinterpret_cast<int16_t *>(stg + (size_t)nitm * A.KW);  // [2][lo, hi][max_nv 9]
+    FF *stg = reinterpret_cast<FF *>(p);                 // [max_nv 9][KW | 1]
+    int16_t *sw = reinterpret_cast<int16_t *>(stg + (size_t)nitm * kw_stride(A.KW));  // [2][lo, hi][max_nv 9]
+    int32_t *srw = reinterpret_cast<int32_t *>(sw + ((4 * nitm + 7) / 8) * 8);          // [2][max_nv 9]
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = w == F32_XW;
     const Geo &g = A.g;
@@ -704,10 +741,16 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
     const int64_t ntau = A.ncolor > blockIdx.x ? (A.ncolor - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t nit = ntau * nch;
     if (nit == 0) return;
+    const unsigned mbar = (unsigned)__cvta_generic_to_shared(p3bar);
+    if (threadIdx.x == 0) mbar_init(mbar, F32_THREADS_ALL);
     {
         const int64_t t0 = A.color_tris[blockIdx.x];
-        if (producer) chunk_setup(A, t0, 0, lane, sub[0]);
-        stage_plan(A, g.F[3 * t0], g.F[3 * t0 + 1], g.F[3 * t0 + 2], 0, sgs[0], sw, sw + nitm);
+        if (producer) {
+            chunk_setup(A, t0, 0, lane, sub[0]);
+            stage_chunk_plan(A, 0, lane, sgs[0]);
+        }
+        __syncthreads();
+        stage_bounds(A, g.F[3 * t0], g.F[3 * t0 + 1], g.F[3 * t0 + 2], sgs[0], sw, sw + nitm, srw);
     }
     __syncthreads();
     int64_t cur_tau = -1;
@@ -717,13 +760,16 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
         const Setup32 &su = sub[bf];
         Stage32 &sg = sgs[bf];
         int16_t *swlo = sw + 2 * nitm * bf, *swhi = swlo + nitm;
+        int32_t *srow = srw + nitm * bf;
         if (producer) {
-            stage_windows(A, su, lane, sg, stg);
+            // the staged windows, this plan's twin and the next setup were read by the previous P3
+            if (it > 0) mbar_wait(mbar, (unsigned)((it - 1) & 1), A.status);
+            stage_windows(A, lane, sg, srow, stg);
             if (it + 1 < nit) {
                 const int64_t t2 = A.color_tris[blockIdx.x + ((it + 1) / nch) * gridDim.x];
+                stage_chunk_plan(A, (it + 1) % nch, lane, sgs[bf ^ 1]);
                 chunk_setup(A, t2, (it + 1) % nch, lane, sub[bf ^ 1]);
             }
-            asm volatile("cp.async.wait_all;" ::: "memory");
         } else {
             if (su.tau != cur_tau) {
                 cur_tau = su.tau;
@@ -731,13 +777,13 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
                 dx1 = g.dq32[(cur_tau * 7 + w) * 3 + 1];
                 dx2 = g.dq32[(cur_tau * 7 + w) * 3 + 2];
             }
-            quad_thread<W>(A, C, su, w, lane, dx0, dx1, dx2, red, rbase);
+            quad_thread<W>(A, C, su, w, lane, dx0, dx1, dx2, red, rbase, mbar, it);
         }
         __syncthreads();  // P1 done: red, rbase, staged windows
-        if (it + 1 < nit) {  // plan of the next chunk (read-only inputs)
-            const int64_t t2 = A.color_tris[blockIdx.x + ((it + 1) / nch) * gridDim.x];
+        if (it + 1 < nit) {  // window bounds of the next chunk (read-only inputs)
+            const Setup32 &sn = sub[bf ^ 1];
             int16_t *nlo = sw + 2 * nitm * (bf ^ 1);
-            stage_plan(A, g.F[3 * t2], g.F[3 * t2 + 1], g.F[3 * t2 + 2], (it + 1) % nch, sgs[bf ^ 1], nlo, nlo + nitm);
+            stage_bounds(A, sn.Ft[0], sn.Ft[1], sn.Ft[2], sgs[bf ^ 1], nlo, nlo + nitm, srw + nitm * (bf ^ 1));
         }
         FF L[ITEMS][9];
         int ubv[ITEMS];
@@ -746,6 +792,7 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
             const int k = threadIdx.x + r * F32_THREADS_ALL;
             if (k < 32 * NU) reduce_item<W>(A, su, red, rbase, k & 31, k >> 5, L[r], ubv[r]);
         }
+        if (producer) asm volatile("cp.async.wait_all;" ::: "memory");  // staged windows landed
         __syncthreads();  // every read of red done: Lb may take its space
 #pragma unroll
         for (int r = 0; r < ITEMS; ++r) {
@@ -758,8 +805,10 @@ far32_kernel(const FarArgs A, const __grid_constant__ ChebLag32 C) {
             }
         }
         __syncthreads();  // Lb, ub written
-        scatter_chunk32<W>(A, su, sg, stg, swlo, swhi, Lb, ub);
-        __syncthreads();  // Lb (red), staged windows and this setup free again
+        scatter_chunk32<W>(A, su, sg, stg, swlo, swhi, srow, Lb, ub);
+        // P3 done for this thread: the next P1 runs on while others finish;
+        // whoever reuses Lb (red), the staging or this setup waits for all
+        mbar_arrive(mbar);
     }
 }
 

@@ -69,6 +69,7 @@ enum {
     ST_WINDOW = 2,         // a vertex-pair lag window exceeded its storage
     ST_NEAR_ORDER = 4,     // near rule too large for shared memory
     ST_NBR = 8,            // near neighbour lookup failed
+    ST_WAIT = 16,          // a bounded wait inside a kernel gave up
 };
 
 // Element-pair record of the bounds pass: kept lag range per lag class and a
@@ -156,6 +157,7 @@ struct FarArgs {
     const int32_t *chunk_vert;
     const int32_t *chunk_sptr;
     const int32_t *chunk_src;  // sigma_local * 3 + corner
+    const int4 *chunk_hdr;     // per chunk: first vertex, vertices, first source, sources
     int64_t nchunks;
     const float *rule_w;       // 7 weights
     const float *rule_l;       // 7 x 3 barycentrics
