@@ -220,13 +220,16 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply(const tdbem_asm *a, const double *
  * device memory to its own pool, or code under a fixed memory budget where
  * an allocation failing halfway through a run is not acceptable. The
  * transposed x goes to a fixed scratch array of 2^21 doubles (16 MiB) in
- * device global memory, reserved when the library's module is loaded; N*M
- * above 2^21 is rejected with TDBEM_E_INVALID_ARG before anything runs. The
- * first call on each device looks up the scratch address (with that device
- * current); make that first call before any stream capture. Nothing has to
- * be zeroed beforehand: every scratch entry that is read is first written.
- * The scratch is shared by all calls on a device, whatever the assembler:
- * calls that overlap in time race on it and must be ordered (one stream).
+ * device global memory; N*M above 2^21 is rejected with TDBEM_E_INVALID_ARG
+ * before anything runs. The runtime reserves that array when it loads the
+ * library's module on a device, which it does lazily at the first call of
+ * this entry point there: a caller that commits all remaining device memory
+ * to its own pool makes one call before doing so, and makes its first call
+ * before any stream capture. The scratch address is looked up (with the
+ * device current) on every call. Nothing has to be zeroed beforehand: every
+ * scratch entry that is read is first written. The scratch is shared by all
+ * calls on a device, whatever the assembler: calls that overlap in time race
+ * on it and must be ordered (one stream).
  * Other arguments, ownership and errors as for tdbem_hessenberg_apply. */
 TDBEM_API tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *a, const double *x_dev, double *y_dev,
                                                       void *stream);
