@@ -252,6 +252,24 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *a, const 
 TDBEM_API tdbem_status tdbem_rhs_assemble(const tdbem_asm *a, int32_t kind, const double *params,
                                           int32_t nparams, double *g_dev, void *stream);
 
+/* Retarded double layer potential (Sec. 2, Eq. RetardedPotential), the
+ * evaluation of a solution off the surface:
+ *   u(x, t) = -1/(4 pi) int_Gamma n_y.(x - y)/r [phi(y, t - r/c)/r^2
+ *             + d_t phi(y, t - r/c)/(c r)] dGamma_y,   r = |x - y|,
+ * for the density phi(y, s) = sum_{k, j} alpha[k M + j] b_k(s) phi_j(y)
+ * (p = 0 time basis, hat functions in space). Every triangle is integrated
+ * by the collapsed Gauss product rule with n points per direction (n^2 per
+ * triangle); FP64. alpha: device, N*M doubles (row k at [k*M, k*M + M));
+ * X: device, P x 3 doubles (points off the surface); times: device, nt
+ * doubles; u: device, P x nt doubles (u[p*nt + i] = u(X_p, times_i)), all
+ * caller-owned. Needs no assembly. The quadrature points and density
+ * coefficients (E n^2 (8 + N) doubles) are allocated through the registered
+ * allocator for the call; synchronises the stream. TDBEM_E_INVALID_ARG for
+ * NULL arrays, P < 0, nt < 1 or n outside 1..32. */
+TDBEM_API tdbem_status tdbem_double_layer(const tdbem_asm *a, const double *alpha_dev, const double *x_dev,
+                                          int64_t P, const double *times_dev, int32_t nt, int32_t n, double *u_dev,
+                                          void *stream);
+
 /* Solve A alpha = g (the block-Hessenberg system of Eq. Apartitioned) by
  * restarted GMRES(restart) (Sec. 4) with tdbem_hessenberg_apply as the
  * product: zero initial guess, stop when ||g - A alpha|| <= tol ||g|| or after

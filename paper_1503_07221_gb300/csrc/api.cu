@@ -1702,6 +1702,33 @@ tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x,
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_double_layer(const tdbem_asm *A, const double *alpha, const double *X, int64_t P,
+                                const double *times, int32_t nt, int32_t n, double *u, void *stream) {
+    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (P < 0 || nt < 1) return fail(TDBEM_E_INVALID_ARG, "need P >= 0 points and nt >= 1 times");
+    if (n < 1 || n > 32) return fail(TDBEM_E_INVALID_ARG, "n (Gauss points per direction) must be in 1..32");
+    if (!alpha || !times || (P > 0 && (!X || !u))) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (A->tg->p != 0) return fail(TDBEM_E_UNSUPPORTED, "the potential takes temporal degree p = 0");
+    if (P == 0) return TDBEM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const tdbem_mesh &m = *A->mesh;
+    const int N = (int)A->tg->N;
+    const int64_t EQ = m.E * (int64_t)n * n;
+    std::vector<double> gx, gw;
+    gauss_legendre01(n, gx, gw);
+    DevBuf dgx, dgw, yw, coef;
+    tdbem_status s;
+    if ((s = upload(dgx, gx, st)) || (s = upload(dgw, gw, st))) return s;
+    if ((s = dev_alloc(yw, (size_t)EQ * 2 * sizeof(double4), st))) return s;
+    if ((s = dev_alloc(coef, (size_t)EQ * N * sizeof(double), st))) return s;
+    Geo g = make_geo(const_cast<tdbem_asm *>(A));
+    CUDA_TRY(launch_double_layer(g, (const double *)A->tgrid.p, N, A->tg->c, (const double *)dgx.p,
+                                 (const double *)dgw.p, n, alpha, X, P, times, nt, (double4 *)yw.p, (double *)coef.p,
+                                 u, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_rhs_assemble(const tdbem_asm *A, int32_t kind, const double *params, int32_t nparams,
                                 double *g_dev, void *stream) {
     if (!A || !g_dev) return fail(TDBEM_E_INVALID_ARG, "NULL argument");

@@ -5,66 +5,9 @@
 #include <math.h>
 
 #include "tdbem_internal.h"
+#include "time_basis.cuh"
 
 namespace tdbem {
-
-// Smooth step of Sec. 3: f(x) = erf(2 artanh x)/2 + 1/2 on |x| < 1, with
-// u = 2 artanh x:  f' = (2/sqrt(pi)) e^{-u^2} / (1 - x^2),
-//                  f'' = (4/sqrt(pi)) e^{-u^2} (x - 2u) / (1 - x^2)^2.
-__device__ static void smooth_step(double x, double &f0, double &f1, double &f2) {
-    if (x <= -1.0) { f0 = 0.0; f1 = 0.0; f2 = 0.0; return; }
-    if (x >= 1.0) { f0 = 1.0; f1 = 0.0; f2 = 0.0; return; }
-    const double u = 2.0 * atanh(x);
-    const double g = (1.0 - x) * (1.0 + x);
-    const double e = exp(-u * u);
-    const double k = 1.1283791670955126;  // 2 / sqrt(pi)
-    f0 = 0.5 * erfc(-u);
-    f1 = k * e / g;
-    f2 = 2.0 * k * e * (x - 2.0 * u) / (g * g);
-}
-
-// Rising cutoff f_j(s) = f(2 (s - t_j)/h - 1), h = t_{j+1} - t_j, and the
-// falling one 1 - f_j(s) = f(-(2 (s - t_j)/h - 1)), each with d/ds, d2/ds2.
-__device__ static void rising(double s, double tj, double h, double out[3]) {
-    double a, b, c;
-    smooth_step(2.0 * (s - tj) / h - 1.0, a, b, c);
-    out[0] = a; out[1] = b * 2.0 / h; out[2] = c * 4.0 / (h * h);
-}
-__device__ static void falling(double s, double tj, double h, double out[3]) {
-    double a, b, c;
-    smooth_step(1.0 - 2.0 * (s - tj) / h, a, b, c);
-    out[0] = a; out[1] = -b * 2.0 / h; out[2] = c * 4.0 / (h * h);
-}
-
-// Time basis function i (0-based) of Eq. BasisFunctions with p = 0 and its
-// first two derivatives at s; causal (zero for s < 0).
-//   i = 0:     8 mu_1 (s/h)^2,   mu_1 = 1 - f_0
-//   inner i:   mu_{i+1} = rho_i, rising on [t_{i-1}, t_i], falling on [t_i, t_{i+1}]
-//   i = N-1:   mu_N = f_{N-2} (1 beyond t_{N-1})
-__device__ static void basis(const double *t, int N, int i, double s, double out[3]) {
-    out[0] = out[1] = out[2] = 0.0;
-    if (s < 0.0) return;
-    double m[3];
-    if (i == 0) {
-        const double h = t[1] - t[0];
-        if (s >= t[1]) return;
-        falling(s, t[0], h, m);
-        const double q = s / h;
-        out[0] = 8.0 * m[0] * q * q;
-        out[1] = 8.0 * m[1] * q * q + 16.0 * m[0] * q / h;
-        out[2] = 8.0 * m[2] * q * q + 32.0 * m[1] * q / h + 16.0 * m[0] / (h * h);
-        return;
-    }
-    if (i == N - 1) {
-        if (s <= t[N - 2]) return;
-        if (s >= t[N - 1]) { out[0] = 1.0; return; }
-        rising(s, t[N - 2], t[N - 1] - t[N - 2], out);
-        return;
-    }
-    if (s <= t[i - 1] || s >= t[i + 1]) return;
-    if (s <= t[i]) rising(s, t[i - 1], t[i] - t[i - 1], out);
-    else falling(s, t[i], t[i + 1] - t[i], out);
-}
 
 __device__ static double left_end(const double *t, int N, int i) { return i == 0 ? 0.0 : t[i - 1]; }
 __device__ static double right_end(const double *t, int N, int i) { return i == N - 1 ? t[N - 1] : t[i + 1]; }

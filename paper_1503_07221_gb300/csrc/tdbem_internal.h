@@ -398,6 +398,12 @@ void launch_gfill(const GradedArgs &a, const int *cb2api, const int64_t *nbr_ptr
 size_t gfar_smem(int max_col_panels, bool fp64);
 void launch_gcoef32(const double *coef, int npan, float *out, cudaStream_t st);
 
+// potential.cu: retarded double layer potential at P points and nt times;
+// workspace yw (E n^2 x 2 double4) and coef (N E n^2 doubles)
+cudaError_t launch_double_layer(const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
+                                int n, const double *alpha, const double *X, int64_t P, const double *times, int nt,
+                                double4 *yw, double *coef, double *out, cudaStream_t st);
+
 // peaks.cu: FMA throughput of the device (roofline denominators)
 cudaError_t measure_fma_peaks(double *fp32, double *fp64, cudaStream_t st);
 // noalloc.cu: fixed scratch of MV_STATIC_MAX doubles for the matvec that

@@ -71,6 +71,7 @@ def lib():
     L.tdbem_hessenberg_apply.argtypes = [vp, vp, vp, vp]
     L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.tdbem_rhs_assemble.argtypes = [vp, i32, vp, i32, vp, vp]
+    L.tdbem_double_layer.argtypes = [vp, vp, vp, i64, vp, i32, i32, vp, vp]
     L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
     L.tdbem_solve_fgmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, vp, C.POINTER(i32),
                                      C.POINTER(C.c_double), vp]
@@ -265,6 +266,19 @@ class Assembler:
         p = np.ascontiguousarray(params, dtype=np.float64)
         _check(lib().tdbem_rhs_assemble(self.h, kind, p.ctypes.data if p.size else None, p.size,
                                         C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
+        return out
+
+    def double_layer(self, alpha, X, times, n=8, out=None, stream=None):
+        """Retarded double layer potential of the density alpha ((N, M)
+        float64 CUDA tensor) at points X ((P, 3) float64 CUDA tensor) and
+        times ((nt,) float64 CUDA tensor): (P, nt) float64 CUDA tensor."""
+        import torch
+        P, nt = X.shape[0], times.shape[0]
+        if out is None:
+            out = torch.empty((P, nt), dtype=torch.float64, device="cuda")
+        _check(lib().tdbem_double_layer(self.h, C.c_void_p(alpha.data_ptr()), C.c_void_p(X.data_ptr()), P,
+                                        C.c_void_p(times.data_ptr()), nt, n, C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(_stream(stream))))
         return out
 
     def solve(self, g, restart=50, tol=1e-10, max_iter=2000, stream=None):
