@@ -182,6 +182,21 @@ TDBEM_API tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *
  * pattern sizes changed. */
 TDBEM_API tdbem_status tdbem_assemble_all(tdbem_asm *a, void *stream);
 
+/* One block (k, i), i <= k+1, of the block-Hessenberg matrix, assembled on
+ * its own from its own psi_{k,i} (Sec. 3, Eq. MatrixEntries; Eq.
+ * SparsitySmallBlock for its pattern), on any time grid: psi table, element-
+ * pair bounds, pattern, far and near quadrature and CSR of this block only,
+ * by the kernels of the non-equidistant path. On an equidistant grid the
+ * result equals the unique block that Eq. relationAtildeBlock maps (k, i) to.
+ * Afterwards tdbem_block_csr, tdbem_block_csr_host and tdbem_block_info with
+ * b = TDBEM_LAST_BLOCK return it (borrowed pointers valid until the next
+ * tdbem_assemble_block call or tdbem_asm_destroy); the assembler's own
+ * blocks are untouched. Synchronises the stream. TDBEM_E_INVALID_ARG for
+ * k or i outside 0..N-1, i > k+1, or a block whose support starts beyond
+ * diam(Gamma) (a zero block). */
+#define TDBEM_LAST_BLOCK (-1)
+TDBEM_API tdbem_status tdbem_assemble_block(tdbem_asm *a, int32_t k, int32_t i, void *stream);
+
 /* CSR of unique block b (borrowed device pointers). which = TDBEM_FAR: M+1
  * int64 row offsets, int32 sorted columns and float (MIXED) / double (FP64)
  * values; TDBEM_NEAR: the near sub-pattern with double values. Any output

@@ -420,7 +420,12 @@ struct tdbem_asm {
         g_pan32_d, g_p64_d, g_kw_d, g_doff_d, g_ndoff_d, g_tkb, g_tib, g_tr0, g_tdr, g_samples, g_coef, g_coef32,
         g_geol, g_cenh, g_cenl, g_coloff_d, g_dense, g_ndense;
     std::vector<cudaEvent_t> g_ev;
+    // one block on its own (tdbem_assemble_block): the planner keeps only
+    // block (only_k, only_i); `single` is the sub-assembler of the last call
+    int only_k = -1, only_i = -1;
+    tdbem_asm *single = nullptr;
     ~tdbem_asm() {
+        delete single;
         for (auto &e : g_ev)
             if (e) cudaEventDestroy(e);
         for (auto &g : gexec)
@@ -522,6 +527,7 @@ static tdbem_status plan_graded(tdbem_asm &A) {
         for (int64_t i = 0; i < N && i <= k + 1; ++i) {
             const double a = std::max(0.0, tl(k) - tr(i)), b = tr(k) - tl(i);
             if (!(b > a) || a >= A.mesh->diam - tie) continue;
+            if (A.only_k >= 0 && (k != A.only_k || i != A.only_i)) continue;
             api_of[k * N + i] = (int)A.blocks.size();
             A.blocks.push_back({(int)k, (int)i, -1, 0, a, b});
         }
@@ -933,6 +939,10 @@ tdbem_status tdbem_num_blocks(const tdbem_asm *a, int64_t *n) {
 tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t *i, int32_t *m2, int32_t *m1,
                               int64_t *nf, int64_t *nn) {
     if (!a) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (b == TDBEM_LAST_BLOCK) {
+        if (!a->single || !a->single->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_block first");
+        return tdbem_block_info(a->single, 0, k, i, m2, m1, nf, nn);
+    }
     if (b < 0 || b >= (int64_t)a->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
     if (k) *k = a->blocks[b].kb;
     if (i) *i = a->blocks[b].ib;
@@ -1573,9 +1583,37 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
     return assemble_body(A, st, false);
 }
 
+tdbem_status tdbem_assemble_block(tdbem_asm *A, int32_t k, int32_t i, void *stream) {
+    if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    const int64_t N = A->tg->N;
+    if (k < 0 || k >= N || i < 0 || i >= N) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
+    if (i > k + 1) return fail(TDBEM_E_INVALID_ARG, "block above the first superdiagonal is zero (i > k + 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!A->single || A->single->only_k != k || A->single->only_i != i) {
+        delete A->single;
+        A->single = nullptr;
+        tdbem_asm *B = new tdbem_asm();
+        B->mesh = A->mesh;
+        B->tg = A->tg;
+        B->opts = A->opts;
+        B->fp64 = A->fp64;
+        B->only_k = k;
+        B->only_i = i;
+        tdbem_status s = create_graded(*B, st);
+        if (!s && B->blocks.empty()) s = fail(TDBEM_E_INVALID_ARG, "block (k, i) is zero: its psi support starts beyond diam");
+        if (s) { delete B; return s; }
+        A->single = B;
+    }
+    return assemble_graded(A->single, st);
+}
+
 tdbem_status tdbem_block_csr(const tdbem_asm *A, int64_t b, int32_t which, const int64_t **rp, const int32_t **col,
                              const void **val, int64_t *nnz) {
     if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (b == TDBEM_LAST_BLOCK) {
+        if (!A->single || !A->single->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_block first");
+        return tdbem_block_csr(A->single, 0, which, rp, col, val, nnz);
+    }
     if (b < 0 || b >= (int64_t)A->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
     if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
     const int64_t M = A->mesh->M;
@@ -1604,6 +1642,7 @@ tdbem_status tdbem_block_csr_host(const tdbem_asm *A, int64_t b, int32_t which, 
     tdbem_status s = tdbem_block_csr(A, b, which, &drp, &dcol, &dval, &nnz);
     if (s) return s;
     const int64_t M = A->mesh->M;
+    if (b == TDBEM_LAST_BLOCK) A = A->single;
     const size_t vs = (which == TDBEM_FAR && !A->fp64) ? 4 : 8;
     if (rp) CUDA_TRY(cudaMemcpy(rp, drp, (M + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     if (col && nnz) CUDA_TRY(cudaMemcpy(col, dcol, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));

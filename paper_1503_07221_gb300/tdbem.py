@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libtdbem.so")
 OK = 0
 RHS_PLANE_WAVE, RHS_SPHERE_N0, RHS_SPHERE_N1 = 0, 1, 2
 E_INVALID_ARG, E_MESH, E_TIMEGRID, E_OOM, E_CUDA, E_DEVICE, E_NOT_ASSEMBLED, E_UNSUPPORTED = range(1, 9)
+LAST_BLOCK = -1
 PREC_FP64 = 0
 PREC_MIXED = 1
 FAR = 0
@@ -66,6 +67,7 @@ def lib():
     L.tdbem_block_info.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                    C.POINTER(i64), C.POINTER(i64)]
     L.tdbem_assemble_all.argtypes = [vp, vp]
+    L.tdbem_assemble_block.argtypes = [vp, i32, i32, vp]
     L.tdbem_block_csr.argtypes = [vp, i64, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
     L.tdbem_block_csr_host.argtypes = [vp, i64, i32, vp, vp, vp]
     L.tdbem_hessenberg_apply.argtypes = [vp, vp, vp, vp]
@@ -190,6 +192,10 @@ class Assembler:
 
     def assemble(self, stream=None):
         _check(lib().tdbem_assemble_all(self.h, C.c_void_p(_stream(stream))))
+
+    def assemble_block(self, k, i, stream=None):
+        """Block (k, i) on its own; read it back with b = LAST_BLOCK."""
+        _check(lib().tdbem_assemble_block(self.h, k, i, C.c_void_p(_stream(stream))))
 
     def num_blocks(self):
         n = C.c_int64()
