@@ -144,14 +144,18 @@ TDBEM_API tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, con
                                int64_t E, tdbem_mesh **out);
 
 /* Time grid of N points (host): t[0] = 0 < t[1] < ... < t[N-1] = T (Sec. 3).
- * p: Legendre degree of the time basis (only 0 in this build); basis_kind: 0
- * = the paper's step f = erf(2 artanh x)/2 + 1/2; c: wave speed (> 0, r =
- * |x-y|/c). An equidistant grid (|t_i - i T/(N-1)| <= 1e-12 T) uses the
+ * p: Legendre degree of the time basis (only 0 in this build); basis_kind:
+ * the smooth step that builds the partition of unity, TDBEM_STEP_ERF_ARTANH
+ * (0) = the paper's f = erf(2 artanh x)/2 + 1/2, TDBEM_STEP_EXP_INV (1) =
+ * F(s) = h(s)/(h(s) + h(1-s)), h(s) = exp(-1/s), s = (x+1)/2 (any other
+ * value: TDBEM_E_INVALID_ARG); c: wave speed (> 0, r = |x-y|/c). An equidistant grid (|t_i - i T/(N-1)| <= 1e-12 T) uses the
  * Toeplitz block reuse of Sec. 5.1; any other grid assembles every nonzero
  * block on its own (the uneven steps enter the basis through the local step
  * widths: b_1 uses t_1 - t_0, inner flanks the widths of their own
  * intervals). The assembler needs 5 <= N <= 1000 and, on a non-equidistant
  * grid, at most 256 nonzero blocks in one block column. */
+#define TDBEM_STEP_ERF_ARTANH 0
+#define TDBEM_STEP_EXP_INV 1
 TDBEM_API tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_t basis_kind,
                                    double c, tdbem_timegrid **out);
 

@@ -47,7 +47,7 @@ def lib():
         L = C.CDLL(path)
         L.or_create.restype = C.c_void_p
         L.or_create.argtypes = [f64p, C.c_int64, i32p, C.c_int64, f64p, C.c_int64,
-                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
         L.or_destroy.argtypes = [C.c_void_p]
         L.or_num_blocks.restype = C.c_int64
         L.or_num_blocks.argtypes = [C.c_void_p]
@@ -56,6 +56,7 @@ def lib():
         L.or_diam.argtypes = [C.c_void_p]
         L.or_tri_geom.argtypes = [C.c_void_p, C.c_int64, f64p]
         L.or_set_first_kind.argtypes = [C.c_void_p, C.c_int]
+        L.or_step.argtypes = [C.c_int, C.c_double, f64p]
         L.or_basis.argtypes = [C.c_void_p, C.c_int, C.c_int, f64p, C.c_int64, f64p]
         L.or_mu.argtypes = [C.c_void_p, C.c_int, f64p, C.c_int64, f64p]
         L.or_psi.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, f64p, C.c_int64, f64p]
@@ -148,15 +149,18 @@ class Oracle:
     """
 
     def __init__(self, verts, tris, t, p=0, equidistant=True, gl_n=32, gl_sub=4,
-                 ss_n=4, psi_mode="interp", interp_S=8, interp_n=32):
+                 ss_n=4, psi_mode="interp", interp_S=8, interp_n=32, basis_kind=0):
         self.V = np.ascontiguousarray(verts, dtype=np.float64)
         self.F = np.ascontiguousarray(tris, dtype=np.int32)
         self.t = np.ascontiguousarray(t, dtype=np.float64)
         self.p = p
         self.equidistant = bool(equidistant)
         mode = {"direct": 0, "interp": 1}[psi_mode]
+        # basis_kind: smooth step of the time basis, 0 erf(2 artanh x) (Sec. 3),
+        # 1 built from exp(-1/s)
         self.h = lib().or_create(self.V, self.V.shape[0], self.F, self.F.shape[0], self.t, self.t.shape[0],
-                                 p, int(equidistant), gl_n, gl_sub, ss_n, mode, interp_S, interp_n)
+                                 p, int(equidistant), gl_n, gl_sub, ss_n, mode, interp_S, interp_n,
+                                 int(basis_kind))
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -12,6 +12,7 @@
  *
  * What it computes, step by step (paper section in brackets):
  *   smooth step f(x) = erf(2 artanh x)/2 + 1/2               [Sec. 3]
+ *     (option: the step of h(s) = e^{-1/s}, s = (x+1)/2, below)
  *   bump / partition of unity mu_i, basis b_{i,m}              [Sec. 3, Eq. BasisFunctions]
  *   psi_{k,i}(r)  = int_0^T  b''_i(t-r) b'_k(t) dt             [Eq. psis]
  *   psi~_{k,i}(r) = int_0^T  b_i(t-r)   b'_k(t) dt             [Eq. psis]
@@ -130,8 +131,9 @@ typedef struct {
     int64_t nblk;
     int32_t *bk, *bi;          /* 0-based test / trial basis index */
     int32_t *bm2, *bm1;        /* temporal orders */
-    or_interp *interp;         /* per block (built lazily when psi_mode==1) */
+    or_interp *interp;         /* per block (built at creation when psi_mode==1) */
     int first_kind;            /* 0: paper's b_1 = 8 mu_1 (t/dt)^2 P_m; 1: mu_1 (test hook) */
+    int basis_kind;            /* smooth step: 0 erf(2 artanh x)/2 + 1/2 (Sec. 3), 1 exp(-1/s) step */
 } orc_t;
 
 static double tl(const orc_t *P, int ib) { return ib == 0 ? 0.0 : P->t[ib - 1]; }
@@ -143,7 +145,7 @@ static double tr(const orc_t *P, int ib) { return ib == P->N - 1 ? P->T : P->t[i
 /*   with u = 2 artanh x: f' = (2/sqrt(pi)) e^{-u^2} / (1-x^2)              */
 /*                        f''= (4/sqrt(pi)) e^{-u^2} (x-2u) / (1-x^2)^2     */
 /* ------------------------------------------------------------------------ */
-static void step_f(double x, double out[3])
+static void step_erf(double x, double out[3])
 {
     if (x <= -1.0) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
     if (x >= 1.0) { out[0] = 1.0; out[1] = 0.0; out[2] = 0.0; return; }
@@ -153,6 +155,37 @@ static void step_f(double x, double out[3])
     out[0] = 0.5 * erfc(-u);
     out[1] = (2.0 / sqrt(OR_PI)) * e / omx2;
     out[2] = (4.0 / sqrt(OR_PI)) * e * (x - 2.0 * u) / (omx2 * omx2);
+}
+
+/* The other smooth step: with s = (x+1)/2 and h(s) = exp(-1/s) (0 for s<=0),
+ *   F(s) = h(s) / (h(s) + h(1-s)).
+ * Differentiating the quotient directly:
+ *   h'(s) = h(s)/s^2,   h''(s) = h(s) (1 - 2 s)/s^4,
+ *   with a = h(s), b = h(1-s): F = a/(a+b),
+ *   F' = (a' b - a b')/(a+b)^2,  b' = -h'(1-s),
+ *   F'' = [(a'' b - a b'')(a+b) - 2 (a' b - a b')(a' + b')]/(a+b)^3,  b'' = h''(1-s),
+ * and d/dx = (1/2) d/ds. Near the ends a or b underflows to 0; then F is 0
+ * or 1 and its derivatives 0 to working precision. */
+static void step_expinv(double x, double out[3])
+{
+    if (x <= -1.0) { out[0] = 0.0; out[1] = 0.0; out[2] = 0.0; return; }
+    if (x >= 1.0) { out[0] = 1.0; out[1] = 0.0; out[2] = 0.0; return; }
+    double s = 0.5 * (x + 1.0), z = 0.5 * (1.0 - x);
+    double a = exp(-1.0 / s), b = exp(-1.0 / z);
+    double den = a + b;
+    if (a == 0.0 || b == 0.0) { out[0] = a == 0.0 ? 0.0 : 1.0; out[1] = 0.0; out[2] = 0.0; return; }
+    double a1 = a / (s * s), b1 = -b / (z * z);
+    double a2 = a * (1.0 - 2.0 * s) / (s * s * s * s), b2 = b * (1.0 - 2.0 * z) / (z * z * z * z);
+    double num1 = a1 * b - a * b1;
+    out[0] = a / den;
+    out[1] = 0.5 * num1 / (den * den);
+    out[2] = 0.25 * ((a2 * b - a * b2) * den - 2.0 * num1 * (a1 + b1)) / (den * den * den);
+}
+
+static void step_f(int kind, double x, double out[3])
+{
+    if (kind == 1) step_expinv(x, out);
+    else step_erf(x, out);
 }
 
 /* Legendre polynomial P_m and its first two derivatives at x */
@@ -185,7 +218,7 @@ static void mu_eval(const orc_t *P, int ib, double s, double out[3])
         if (s >= t[1]) return;
         double h = t[1] - t[0];
         /* 1 - f(x) = f(-x) (erf is odd): no cancellation near the top */
-        step_f(-(2.0 * (s - t[0]) / h - 1.0), f);
+        step_f(P->basis_kind, -(2.0 * (s - t[0]) / h - 1.0), f);
         out[0] = f[0];
         out[1] = -f[1] * (2.0 / h);
         out[2] = f[2] * (4.0 / (h * h));
@@ -195,7 +228,7 @@ static void mu_eval(const orc_t *P, int ib, double s, double out[3])
         if (s <= t[N - 2]) return;
         if (s >= t[N - 1]) { out[0] = 1.0; return; }
         double h = t[N - 1] - t[N - 2];
-        step_f(2.0 * (s - t[N - 2]) / h - 1.0, f);
+        step_f(P->basis_kind, 2.0 * (s - t[N - 2]) / h - 1.0, f);
         out[0] = f[0];
         out[1] = f[1] * (2.0 / h);
         out[2] = f[2] * (4.0 / (h * h));
@@ -204,13 +237,13 @@ static void mu_eval(const orc_t *P, int ib, double s, double out[3])
     if (s <= t[ib - 1] || s >= t[ib + 1]) return;
     if (s <= t[ib]) {
         double h = t[ib] - t[ib - 1];
-        step_f(2.0 * (s - t[ib - 1]) / h - 1.0, f);
+        step_f(P->basis_kind, 2.0 * (s - t[ib - 1]) / h - 1.0, f);
         out[0] = f[0];
         out[1] = f[1] * (2.0 / h);
         out[2] = f[2] * (4.0 / (h * h));
     } else {
         double h = t[ib + 1] - t[ib];
-        step_f(-(2.0 * (s - t[ib]) / h - 1.0), f);
+        step_f(P->basis_kind, -(2.0 * (s - t[ib]) / h - 1.0), f);
         out[0] = f[0];
         out[1] = -f[1] * (2.0 / h);
         out[2] = f[2] * (4.0 / (h * h));
@@ -751,7 +784,8 @@ static void pair_near(const orc_t *P, int64_t s, int64_t q, int n, const double 
 /* Public API                                                                */
 /* ------------------------------------------------------------------------ */
 void *or_create(const double *V, int64_t M, const int32_t *F, int64_t E, const double *t, int64_t N,
-                int p, int equidistant, int gl_n, int gl_sub, int ss_n, int psi_mode, int interp_S, int interp_n)
+                int p, int equidistant, int gl_n, int gl_sub, int ss_n, int psi_mode, int interp_S, int interp_n,
+                int basis_kind)
 {
     orc_t *P = (orc_t *)calloc(1, sizeof(orc_t));
     P->M = M; P->E = E; P->N = N; P->p = p;
@@ -789,6 +823,7 @@ void *or_create(const double *V, int64_t M, const int32_t *F, int64_t E, const d
     P->ss_x = (double *)malloc(sizeof(double) * ss_n); P->ss_w = (double *)malloc(sizeof(double) * ss_n);
     gauss_legendre01(ss_n, P->ss_x, P->ss_w);
     P->psi_mode = psi_mode; P->interp_S = interp_S; P->interp_n = interp_n;
+    P->basis_kind = basis_kind;
     /* diameter = max vertex distance */
     double dm = 0.0;
     for (int64_t i = 0; i < M; ++i)
@@ -877,6 +912,8 @@ void or_tri_geom(void *h, int64_t e, double *out13)
 }
 
 void or_set_first_kind(void *h, int kind) { ((orc_t *)h)->first_kind = kind; }
+/* the smooth step of the given kind and its first two derivatives at x */
+void or_step(int kind, double x, double *out) { step_f(kind, x, out); }
 
 void or_basis(void *h, int ib, int m, const double *s, int64_t n, double *out /* n*3 */)
 {

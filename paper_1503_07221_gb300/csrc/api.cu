@@ -747,7 +747,7 @@ tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_
     for (int64_t i = 1; i < N; ++i)
         if (!(t[i] > t[i - 1]) || !std::isfinite(t[i])) return fail(TDBEM_E_TIMEGRID, "t must be finite and strictly increasing");
     if (p != 0) return fail(TDBEM_E_UNSUPPORTED, "this build takes temporal degree p = 0");
-    if (kind != 0) return fail(TDBEM_E_UNSUPPORTED, "this build takes basis_kind 0 (erf(2 artanh))");
+    if (kind != 0 && kind != 1) return fail(TDBEM_E_INVALID_ARG, "basis_kind must be 0 (erf(2 artanh)) or 1 (exp(-1/s))");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(TDBEM_E_INVALID_ARG, "wave speed must be positive");
     tdbem_timegrid *g = new tdbem_timegrid();
     g->N = N;
@@ -1057,11 +1057,11 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     CUDA_TRY(cudaMemsetAsync(A->ndense_spec.p, 0, A->ndense_spec.n, st));
     // ---- psi tables (FP64 samples, Chebyshev coefficients)
     const int n1 = TOTAL_PANELS, n4 = TOTAL_PANELS * A->S64;
-    launch_psi_samples((const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p,
+    launch_psi_samples(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p,
                        (const int *)A->tab_ib.p, (const double *)A->tab_r0.p, A->tg->dt, 1, n1,
                        (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 8, (double *)A->tab_samples.p, st);
     launch_psi_dct((const double *)A->tab_samples.p, n1, (double *)A->tab_coef1.p, st);
-    launch_psi_samples((const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p + n1,
+    launch_psi_samples(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, nullptr, (const int *)A->tab_kb.p + n1,
                        (const int *)A->tab_ib.p + n1, (const double *)A->tab_r0.p + n1, A->tg->dt / A->S64, A->S64,
                        n4, (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 8,
                        (double *)A->tab_samples.p + (size_t)n1 * NCHEB * 2, st);
@@ -1431,10 +1431,10 @@ static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
     CUDA_TRY(cudaMemsetAsync(A->status.p, 0, 16, st));
     // ---- psi tables: FP32 set (24-point Gauss-Legendre x 4 per piece), FP64 sets (x 8), DCT
     const int nj32 = A->g_njob32, nj64 = A->g_nset64;
-    launch_psi_samples_var((const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p, (const int *)A->g_tib.p,
+    launch_psi_samples_var(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p, (const int *)A->g_tib.p,
                            (const double *)A->g_tr0.p, (const double *)A->g_tdr.p, nj32, (const double *)A->gl_x.p,
                            (const double *)A->gl_w.p, 24, 4, (double *)A->g_samples.p, st);
-    launch_psi_samples_var((const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p + nj32,
+    launch_psi_samples_var(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p + nj32,
                            (const int *)A->g_tib.p + nj32, (const double *)A->g_tr0.p + nj32,
                            (const double *)A->g_tdr.p + nj32, nj64, (const double *)A->gl_x.p,
                            (const double *)A->gl_w.p, 24, 8, (double *)A->g_samples.p + (size_t)nj32 * NCHEB * 2, st);
@@ -1761,7 +1761,7 @@ tdbem_status tdbem_double_layer(const tdbem_asm *A, const double *alpha, const d
     if ((s = dev_alloc(yw, (size_t)EQ * 2 * sizeof(double4), st))) return s;
     if ((s = dev_alloc(coef, (size_t)EQ * N * sizeof(double), st))) return s;
     Geo g = make_geo(const_cast<tdbem_asm *>(A));
-    CUDA_TRY(launch_double_layer(g, (const double *)A->tgrid.p, N, A->tg->c, (const double *)dgx.p,
+    CUDA_TRY(launch_double_layer(A->tg->kind, g, (const double *)A->tgrid.p, N, A->tg->c, (const double *)dgx.p,
                                  (const double *)dgw.p, n, alpha, X, P, times, nt, (double4 *)yw.p, (double *)coef.p,
                                  u, st));
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1787,7 +1787,7 @@ tdbem_status tdbem_rhs_assemble(const tdbem_asm *A, int32_t kind, const double *
     }
     const tdbem_asm *Ac = A;
     Geo g = make_geo(const_cast<tdbem_asm *>(Ac));
-    launch_rhs(g, (const double *)A->tgrid.p, (int)A->tg->N, A->tg->c, (const double *)A->rule_w64.p,
+    launch_rhs(A->tg->kind, g, (const double *)A->tgrid.p, (int)A->tg->N, A->tg->c, (const double *)A->rule_w64.p,
                (const double *)A->rule_l64.p, (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 4, kind, prm,
                g_dev, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());

@@ -58,18 +58,8 @@ __global__ void dl_coef_kernel(const Geo g, const double *gx, int n, int N, cons
     coef[id] = (1.0 - u) * a[g.F[3 * e]] + u * (1.0 - v) * a[g.F[3 * e + 1]] + u * v * a[g.F[3 * e + 2]];
 }
 
-// f(x) and f(-x) of the smooth step, and f'(x) (= f'(-x))
-__device__ static inline void step_pair(double x, double &fr, double &ff, double &d1) {
-    if (x <= -1.0) { fr = 0.0; ff = 1.0; d1 = 0.0; return; }
-    if (x >= 1.0) { fr = 1.0; ff = 0.0; d1 = 0.0; return; }
-    const double u = 2.0 * atanh(x);
-    fr = 0.5 * erfc(-u);
-    ff = 0.5 * erfc(u);
-    d1 = 1.1283791670955126 * exp(-u * u) / ((1.0 - x) * (1.0 + x));
-}
-
 __global__ void __launch_bounds__(DL_THREADS)
-dl_eval_kernel(const double *X, int64_t P, const double *times, int nt, double c, const double *tg, int N,
+dl_eval_kernel(int bkind, const double *X, int64_t P, const double *times, int nt, double c, const double *tg, int N,
                const double4 *yw, const double *coef, int64_t EQ, double *out) {
     __shared__ double4 sy[DL_TILE], sw[DL_TILE];
     __shared__ double st[1024];
@@ -110,8 +100,8 @@ dl_eval_kernel(const double *X, int64_t P, const double *times, int nt, double c
                     else hi = mid;
                 }
                 const double h = st[lo + 1] - st[lo];
-                double fr, ff, f1;
-                step_pair(2.0 * (s - st[lo]) / h - 1.0, fr, ff, f1);
+                double fr, ff, f1, f2;
+                smooth_step2(bkind, 2.0 * (s - st[lo]) / h - 1.0, fr, ff, f1, f2);
                 const double df = f1 * 2.0 / h;
                 // b_lo falls (times 8 (s/h)^2 for the first function), b_lo+1 rises
                 double b0 = ff, db0 = -df;
@@ -130,7 +120,7 @@ dl_eval_kernel(const double *X, int64_t P, const double *times, int nt, double c
     if (act) out[id] = -acc * 0.079577471545947668;  // 1 / (4 pi)
 }
 
-cudaError_t launch_double_layer(const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
+cudaError_t launch_double_layer(int bkind, const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
                                 int n, const double *alpha, const double *X, int64_t P, const double *times, int nt,
                                 double4 *yw, double *coef, double *out, cudaStream_t st) {
     const int64_t EQ = g.E * (int64_t)n * n;
@@ -139,7 +129,7 @@ cudaError_t launch_double_layer(const Geo &g, const double *tg, int N, double c,
     const int64_t nth = P * nt;
     if (nth > 0)
         dl_eval_kernel<<<(unsigned)((nth + DL_THREADS - 1) / DL_THREADS), DL_THREADS, 0, st>>>(
-            X, P, times, nt, c, tg, N, yw, coef, EQ, out);
+            bkind, X, P, times, nt, c, tg, N, yw, coef, EQ, out);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,7 @@ __device__ static double right_end(const double *t, int N, int i) { return i == 
 // psi_{k,i}(r) and psi~_{k,i}(r) of Eq. psis: integrate over the overlap of
 // the test support and the shifted trial support, split at the interior
 // breakpoints t_k and t_i + r, composite Gauss-Legendre on each piece.
-__device__ static void psi_direct(const double *t, int N, int kb, int ib, double r,
+__device__ static void psi_direct(int bkind, const double *t, int N, int kb, int ib, double r,
                                   const double *gx, const double *gw, int gn, int gsub,
                                   double &psi, double &psit) {
     psi = 0.0; psit = 0.0;
@@ -38,8 +38,8 @@ __device__ static void psi_direct(const double *t, int N, int kb, int ib, double
             for (int g = 0; g < gn; ++g) {
                 const double tt = a0 + w * gx[g];
                 double bk[3], bi[3];
-                basis(t, N, kb, tt, bk);
-                basis(t, N, ib, tt - r, bi);
+                basis(bkind, t, N, kb, tt, bk);
+                basis(bkind, t, N, ib, tt - r, bi);
                 s0 += w * gw[g] * bi[2] * bk[1];
                 s1 += w * gw[g] * bi[0] * bk[1];
             }
@@ -52,7 +52,7 @@ __device__ static void psi_direct(const double *t, int N, int kb, int ib, double
 // One thread per (sub-panel, Chebyshev node). Sub-panel p covers
 // r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]); with pdr given, its
 // width is pdr[p] instead (uneven panels of a graded grid).
-__global__ void psi_samples_kernel(const double *t, int N, const int *pkb, const int *pib,
+__global__ void psi_samples_kernel(int bkind, const double *t, int N, const int *pkb, const int *pib,
                                    const double *pr0, double dr, const double *pdr, int total, const double *gx,
                                    const double *gw, int gn, int gsub, double *samples) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -62,7 +62,7 @@ __global__ void psi_samples_kernel(const double *t, int N, const int *pkb, const
     const double w = pdr ? pdr[p] : dr;
     const double r = pr0[p] + 0.5 * w * (xm + 1.0);
     double a, b;
-    psi_direct(t, N, pkb[p], pib[p], r, gx, gw, gn, gsub, a, b);
+    psi_direct(bkind, t, N, pkb[p], pib[p], r, gx, gw, gn, gsub, a, b);
     samples[2 * id + 0] = a;
     samples[2 * id + 1] = b;
 }
@@ -84,23 +84,23 @@ __global__ void psi_dct_kernel(const double *samples, int total, double *coef) {
     coef[2 * id + 1] = s1 * sc;
 }
 
-void launch_psi_samples(const double *t, int N, const int *panel_class, const int *panel_kb,
+void launch_psi_samples(int bkind, const double *t, int N, const int *panel_class, const int *panel_kb,
                         const int *panel_ib, const double *panel_r0, double panel_dr, int S,
                         int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                         double *samples, cudaStream_t st) {
     (void)panel_class; (void)S;
     const int n = total_sub * NCHEB;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(t, N, panel_kb, panel_ib, panel_r0,
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_r0,
                                                        panel_dr, nullptr, total_sub, gl_x, gl_w, gl_n,
                                                        gl_sub, samples);
 }
 
-void launch_psi_samples_var(const double *t, int N, const int *panel_kb, const int *panel_ib,
+void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_kb, const int *panel_ib,
                             const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
                             const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st) {
     const int n = total_sub * NCHEB;
     if (n <= 0) return;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(t, N, panel_kb, panel_ib, panel_r0, 0.0, panel_dr,
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_r0, 0.0, panel_dr,
                                                        total_sub, gl_x, gl_w, gl_n, gl_sub, samples);
 }
 
@@ -131,7 +131,7 @@ __device__ static double rhs_data(int kind, const double *prm, const double *x, 
 // One thread per (time index k, vertex l): the triangles around l, 7 points
 // each, and the support of bdot_k split at every grid point into `sub`
 // panels of gn Gauss-Legendre points (FP64).
-__global__ void rhs_kernel(Geo g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+__global__ void rhs_kernel(int bkind, Geo g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
                            const double *gx, const double *gw, int gn, int sub, int kind, RhsParams prm,
                            double *out) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,7 +154,7 @@ __global__ void rhs_kernel(Geo g, const double *t, int N, double c, const double
                     for (int m = 0; m < gn; ++m) {
                         const double s = t[j] + (sb + gx[m]) * h;
                         double b[3];
-                        basis(t, N, k, s, b);
+                        basis(bkind, t, N, k, s, b);
                         it += gw[m] * h * b[1] * rhs_data(kind, prm.p, x, geo, s / c);
                     }
             }
@@ -164,11 +164,11 @@ __global__ void rhs_kernel(Geo g, const double *t, int N, double c, const double
     out[id] = acc;
 }
 
-void launch_rhs(const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+void launch_rhs(int bkind, const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
                 const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
                 cudaStream_t st) {
     const int64_t n = (int64_t)N * g.M;
-    rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(g, t, N, c, rule_w, rule_l, gx, gw, gn, sub, kind, prm,
+    rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bkind, g, t, N, c, rule_w, rule_l, gx, gw, gn, sub, kind, prm,
                                                           out);
 }
 

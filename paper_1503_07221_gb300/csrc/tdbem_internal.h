@@ -114,13 +114,14 @@ struct alignas(8) ChebLag32 {
 
 // ---- launchers (defined in the .cu files) --------------------------------
 // table.cu
-void launch_psi_samples(const double *t, int N, const int *panel_class, const int *panel_kb,
+// bkind: step function of the time basis (0 erf(2 artanh), 1 exp(-1/s))
+void launch_psi_samples(int bkind, const double *t, int N, const int *panel_class, const int *panel_kb,
                         const int *panel_ib, const double *panel_r0, double panel_dr, int S,
                         int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                         double *samples, cudaStream_t st);
 void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st);
 // sub-panel p covers [r0[p], r0[p] + dr[p]] (uneven panels)
-void launch_psi_samples_var(const double *t, int N, const int *panel_kb, const int *panel_ib,
+void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_kb, const int *panel_ib,
                             const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
                             const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st);
 
@@ -245,7 +246,7 @@ enum { RHS_PLANE_WAVE = 0, RHS_SPHERE_N0 = 1, RHS_SPHERE_N1 = 2 };
 struct RhsParams {
     double p[5];
 };
-void launch_rhs(const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
+void launch_rhs(int bkind, const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
                 const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
                 cudaStream_t st);
 // solve.cu: vector kernels of the GMRES solver
@@ -400,7 +401,7 @@ void launch_gcoef32(const double *coef, int npan, float *out, cudaStream_t st);
 
 // potential.cu: retarded double layer potential at P points and nt times;
 // workspace yw (E n^2 x 2 double4) and coef (N E n^2 doubles)
-cudaError_t launch_double_layer(const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
+cudaError_t launch_double_layer(int bkind, const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
                                 int n, const double *alpha, const double *X, int64_t P, const double *times, int nt,
                                 double4 *yw, double *coef, double *out, cudaStream_t st);
 
