@@ -271,6 +271,20 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *a, const 
 TDBEM_API tdbem_status tdbem_rhs_assemble(const tdbem_asm *a, int32_t kind, const double *params,
                                           int32_t nparams, double *g_dev, void *stream);
 
+/* The assembler's own Chebyshev table of psi and psi~ (Sec. 3.1) for unique
+ * block b of an equidistant grid, evaluated at n distances r (device array)
+ * into out (device, n x 2: psi, psi~), so that the table can be compared
+ * with a direct 1-D quadrature of Eq. psis. which: 0 = the FP64 set (4
+ * sub-panels of degree 32 per time step, used by the near field and the
+ * FP64 path), 1 = the FP32 set (one panel of degree 32 per time step with
+ * the FP32 residuals of the leading coefficients, used by the mixed far
+ * field; summed here in FP64). Zero outside the support. Valid after an
+ * assembly; asynchronous on `stream`. TDBEM_E_UNSUPPORTED on a graded grid
+ * (its tables are per block and panel), TDBEM_E_NOT_ASSEMBLED before an
+ * assembly, TDBEM_E_INVALID_ARG for a bad block, `which` or pointer. */
+TDBEM_API tdbem_status tdbem_psi_table(const tdbem_asm *a, int64_t b, int32_t which, const double *r_dev,
+                                       int64_t n, double *out_dev, void *stream);
+
 /* Retarded double layer potential (Sec. 2, Eq. RetardedPotential), the
  * evaluation of a solution off the surface:
  *   u(x, t) = -1/(4 pi) int_Gamma n_y.(x - y)/r [phi(y, t - r/c)/r^2

@@ -68,6 +68,8 @@ def lib():
         L.or_gauss_legendre.argtypes = [C.c_int, f64p, f64p]
         L.or_pair_local.argtypes = [C.c_void_p, C.c_int64, C.c_int64, i64p, C.c_int, C.c_int, C.c_int, f64p]
         L.or_pattern_counts.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64, i64p]
+        L.or_pattern_hash.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64,
+                                      np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS"), i64p]
         L.or_assemble_rows.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64, i64p, i32p, f64p, f64p]
         L.or_num_threads.restype = C.c_int
         _lib = L
@@ -248,6 +250,17 @@ class Oracle:
         counts = np.zeros(rows.size * blks.size, np.int64)
         lib().or_pattern_counts(self.h, rows, rows.size, blks, blks.size, counts)
         return counts.reshape(blks.size, rows.size)
+
+    def pattern_hash(self, blks, rows=None):
+        """Fingerprint of the patterns of blocks `blks` over rows `rows` (all
+        rows by default): (hash uint64[nb], nnz int64[nb]), hash the sum mod
+        2^64 of splitmix64(l M + j) over the entries (l, j)."""
+        rows = np.arange(self.M, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+        blks = np.ascontiguousarray(blks, dtype=np.int64)
+        hs = np.zeros(blks.size, np.uint64)
+        nz = np.zeros(blks.size, np.int64)
+        lib().or_pattern_hash(self.h, rows, rows.size, blks, blks.size, hs, nz)
+        return hs, nz
 
     def assemble_rows(self, rows, blks):
         """Rows `rows` of blocks `blks`: dict blk -> list over rows of

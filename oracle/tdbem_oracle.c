@@ -1088,6 +1088,52 @@ void or_pattern_counts(void *h, const int64_t *rows, int64_t nrows, const int64_
     }
 }
 
+/* Pattern fingerprint of rows x blocks: per block, the number of structural
+ * entries and the sum mod 2^64 of splitmix64(l M + j) over its entries (l, j)
+ * in the given rows -- the output function of Steele, Lea and Flood's
+ * SplitMix64 as published. A sum does not depend on the order of the rows or
+ * threads, and two patterns with the same count and sum are the same pattern
+ * but for a 2^-64 coincidence. */
+static uint64_t splitmix64_out(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+void or_pattern_hash(void *h, const int64_t *rows, int64_t nrows, const int64_t *blks, int64_t nb, uint64_t *hash,
+                     int64_t *nnz)
+{
+    orc_t *P = (orc_t *)h;
+    for (int64_t b = 0; b < nb; ++b) { hash[b] = 0; nnz[b] = 0; }
+#pragma omp parallel
+    {
+        rowscratch S;
+        S.m = (double *)malloc(sizeof(double) * P->E);
+        S.Mx = (double *)malloc(sizeof(double) * P->E);
+        S.dmin = (double *)malloc(sizeof(double) * P->E * P->maxval);
+        S.dmax = (double *)malloc(sizeof(double) * P->E * P->maxval);
+        double *mind = (double *)malloc(sizeof(double) * P->M), *maxd = (double *)malloc(sizeof(double) * P->M);
+        int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * P->M);
+        uint64_t *hs = (uint64_t *)calloc(nb, sizeof(uint64_t));
+        int64_t *ns = (int64_t *)calloc(nb, sizeof(int64_t));
+#pragma omp for schedule(dynamic)
+        for (int64_t r = 0; r < nrows; ++r) {
+            int64_t l = rows[r];
+            row_bounds(P, l, &S);
+            vertex_bounds(P, &S, mind, maxd);
+            for (int64_t b = 0; b < nb; ++b) {
+                int64_t c = row_pattern(P, blks[b], &S, mind, maxd, cols);
+                for (int64_t q = 0; q < c; ++q) hs[b] += splitmix64_out((uint64_t)l * (uint64_t)P->M + (uint64_t)cols[q]);
+                ns[b] += c;
+            }
+        }
+#pragma omp critical
+        for (int64_t b = 0; b < nb; ++b) { hash[b] += hs[b]; nnz[b] += ns[b]; }
+        free(S.m); free(S.Mx); free(S.dmin); free(S.dmax); free(mind); free(maxd); free(cols); free(hs); free(ns);
+    }
+}
+
 /* assemble rows x blocks. offsets[b*nrows + r] = start of that (block,row)
  * segment in cols/vfar/vnear (lengths from or_pattern_counts). Values are
  * split into the far part (7-point rule on pairs without a shared vertex)

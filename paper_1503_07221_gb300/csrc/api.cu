@@ -1741,6 +1741,23 @@ tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x,
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_psi_table(const tdbem_asm *A, int64_t b, int32_t which, const double *r, int64_t n, double *out,
+                             void *stream) {
+    if (!A || (n > 0 && (!r || !out))) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(TDBEM_E_INVALID_ARG, "n < 0");
+    if (b < 0 || b >= (int64_t)A->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
+    if (which != 0 && which != 1) return fail(TDBEM_E_INVALID_ARG, "which must be 0 (FP64 set) or 1 (FP32 set)");
+    if (A->graded) return fail(TDBEM_E_UNSUPPORTED, "per-class tables exist on equidistant grids only");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "the tables are built by tdbem_assemble_all");
+    const Block &B = A->blocks[b];
+    int panel0 = 0;
+    for (int c = 0; c < B.cls; ++c) panel0 += A->cls_P[c];
+    launch_psi_table(r, n, 1.0 / A->tg->dt, B.lag, A->cls_rho[B.cls], A->cls_P[B.cls], panel0, A->S64,
+                     (const double *)A->tab_coef4.p, A->c32, which, out, (cudaStream_t)stream);
+    CUDA_TRY(cudaGetLastError());
+    return TDBEM_OK;
+}
+
 tdbem_status tdbem_double_layer(const tdbem_asm *A, const double *alpha, const double *X, int64_t P,
                                 const double *times, int32_t nt, int32_t n, double *u, void *stream) {
     if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
@@ -1755,15 +1772,16 @@ tdbem_status tdbem_double_layer(const tdbem_asm *A, const double *alpha, const d
     const int64_t EQ = m.E * (int64_t)n * n;
     std::vector<double> gx, gw;
     gauss_legendre01(n, gx, gw);
-    DevBuf dgx, dgw, yw, coef;
+    DevBuf dgx, dgw, yw, coef, tab;
     tdbem_status s;
     if ((s = upload(dgx, gx, st)) || (s = upload(dgw, gw, st))) return s;
     if ((s = dev_alloc(yw, (size_t)EQ * 2 * sizeof(double4), st))) return s;
     if ((s = dev_alloc(coef, (size_t)EQ * N * sizeof(double), st))) return s;
+    if ((s = dev_alloc(tab, (size_t)DL_TABLE_NODES * sizeof(double3), st))) return s;
     Geo g = make_geo(const_cast<tdbem_asm *>(A));
-    CUDA_TRY(launch_double_layer(A->tg->kind, g, (const double *)A->tgrid.p, N, A->tg->c, (const double *)dgx.p,
-                                 (const double *)dgw.p, n, alpha, X, P, times, nt, (double4 *)yw.p, (double *)coef.p,
-                                 u, st));
+    CUDA_TRY(launch_double_layer(A->tg->kind, g, (const double *)A->tgrid.p, N, A->tg->equidistant ? 1 : 0,
+                                 A->tg->c, (const double *)dgx.p, (const double *)dgw.p, n, alpha, X, P, times, nt,
+                                 (double4 *)yw.p, (double *)coef.p, (double3 *)tab.p, u, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return TDBEM_OK;
 }

@@ -104,6 +104,54 @@ void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_
                                                        total_sub, gl_x, gl_w, gl_n, gl_sub, samples);
 }
 
+// Evaluation of one block's table at distances r (thread per r): the block
+// of lag d in a class with prototype panels [rho, rho + P) in q = r / dt reads
+// panel floor(q - d - rho); the FP64 set has S sub-panels per panel (c64),
+// the FP32 set one (c32 with the FP32 residuals of the leading coefficients,
+// summed here in FP64 so that only the table itself is measured).
+__global__ void psi_table_kernel(const double *r, int64_t n, double inv_dt, int lag, int rho, int P, int panel0,
+                                 int S, const double *c64, const ChebF32 c32, int use32, double *out) {
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const double z = r[id] * inv_dt - lag - rho;
+    double a = 0.0, b = 0.0;
+    if (z > 0.0 && z < (double)P) {
+        const int p = min((int)floor(z), P - 1);
+        double f = z - p;
+        int sub = 0;
+        if (!use32) {
+            sub = min((int)floor(f * S), S - 1);
+            f = f * S - sub;
+        }
+        const double x = 2.0 * f - 1.0;
+        double tm = 1.0, t = x;
+        for (int k = 0; k < NCHEB; ++k) {
+            double ca, cb;
+            if (use32) {
+                ca = (double)c32.c[panel0 + p][k][0] + (k < NCHEB_LO ? (double)c32.lo[panel0 + p][k][0] : 0.0);
+                cb = (double)c32.c[panel0 + p][k][1] + (k < NCHEB_LO ? (double)c32.lo[panel0 + p][k][1] : 0.0);
+            } else {
+                const double *c = c64 + ((size_t)((panel0 + p) * S + sub) * NCHEB + k) * 2;
+                ca = c[0];
+                cb = c[1];
+            }
+            const double tk = k == 0 ? 1.0 : (k == 1 ? x : 2.0 * x * t - tm);
+            if (k >= 2) { tm = t; t = tk; }
+            a += ca * tk;
+            b += cb * tk;
+        }
+    }
+    out[2 * id] = a;
+    out[2 * id + 1] = b;
+}
+
+void launch_psi_table(const double *r, int64_t n, double inv_dt, int lag, int rho, int P, int panel0, int S,
+                      const double *c64, const ChebF32 &c32, int use32, double *out, cudaStream_t st) {
+    if (n <= 0) return;
+    psi_table_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(r, n, inv_dt, lag, rho, P, panel0, S, c64, c32,
+                                                                 use32, out);
+}
+
 void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st) {
     const int n = total_sub * NCHEB;
     psi_dct_kernel<<<(n + 127) / 128, 128, 0, st>>>(samples, total_sub, coef);

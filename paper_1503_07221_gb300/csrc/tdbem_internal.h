@@ -120,6 +120,9 @@ void launch_psi_samples(int bkind, const double *t, int N, const int *panel_clas
                         int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                         double *samples, cudaStream_t st);
 void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStream_t st);
+// evaluation of one block's table (lag, class panels) at n distances: out n x 2
+void launch_psi_table(const double *r, int64_t n, double inv_dt, int lag, int rho, int P, int panel0, int S,
+                      const double *c64, const ChebF32 &c32, int use32, double *out, cudaStream_t st);
 // sub-panel p covers [r0[p], r0[p] + dr[p]] (uneven panels)
 void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_kb, const int *panel_ib,
                             const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
@@ -400,10 +403,13 @@ size_t gfar_smem(int max_col_panels, bool fp64);
 void launch_gcoef32(const double *coef, int npan, float *out, cudaStream_t st);
 
 // potential.cu: retarded double layer potential at P points and nt times;
-// workspace yw (E n^2 x 2 double4) and coef (N E n^2 doubles)
-cudaError_t launch_double_layer(int bkind, const Geo &g, const double *tg, int N, double c, const double *gx, const double *gw,
-                                int n, const double *alpha, const double *X, int64_t P, const double *times, int nt,
-                                double4 *yw, double *coef, double *out, cudaStream_t st);
+// workspace yw (E n^2 x 2 double4), coef (N E n^2 doubles) and the step
+// table tab (DL_TABLE_NODES double3); equi: the grid is equidistant
+constexpr int DL_TABLE_NODES = 1025;
+cudaError_t launch_double_layer(int bkind, const Geo &g, const double *tg, int N, int equi, double c, const double *gx,
+                                const double *gw, int n, const double *alpha, const double *X, int64_t P,
+                                const double *times, int nt, double4 *yw, double *coef, double3 *tab, double *out,
+                                cudaStream_t st);
 
 // peaks.cu: FMA throughput of the device (roofline denominators)
 cudaError_t measure_fma_peaks(double *fp32, double *fp64, cudaStream_t st);

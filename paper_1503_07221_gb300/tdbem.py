@@ -74,6 +74,7 @@ def lib():
     L.tdbem_hessenberg_apply_noalloc.argtypes = [vp, vp, vp, vp]
     L.tdbem_rhs_assemble.argtypes = [vp, i32, vp, i32, vp, vp]
     L.tdbem_double_layer.argtypes = [vp, vp, vp, i64, vp, i32, i32, vp, vp]
+    L.tdbem_psi_table.argtypes = [vp, i64, i32, vp, i64, vp, vp]
     L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
     L.tdbem_solve_fgmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, vp, C.POINTER(i32),
                                      C.POINTER(C.c_double), vp]
@@ -272,6 +273,16 @@ class Assembler:
         p = np.ascontiguousarray(params, dtype=np.float64)
         _check(lib().tdbem_rhs_assemble(self.h, kind, p.ctypes.data if p.size else None, p.size,
                                         C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
+        return out
+
+    def psi_table(self, b, r, which=0, stream=None):
+        """The assembler's psi / psi~ table of unique block b at distances r
+        (float64 CUDA tensor): (n, 2) float64 CUDA tensor; which 0 = FP64 set,
+        1 = FP32 set."""
+        import torch
+        out = torch.empty((r.shape[0], 2), dtype=torch.float64, device="cuda")
+        _check(lib().tdbem_psi_table(self.h, b, which, C.c_void_p(r.data_ptr()), r.shape[0],
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(_stream(stream))))
         return out
 
     def double_layer(self, alpha, X, times, n=8, out=None, stream=None):

@@ -9,6 +9,7 @@ block-Hessenberg product against the oracle's.
 import numpy as np
 import pytest
 
+from _pattern_fingerprint import device_fingerprint
 from paper_1503_07221_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -130,8 +131,10 @@ def test_graded_deterministic(td):
 def test_torus8192_graded_fullsize(td):
     """The batched uneven-block workload at full size (torus 8192 triangles,
     96 graded steps of ratio 1.02 on [0, 6], mixed precision), in the launch
-    configuration bench.py times: row lengths of every block on 32 sampled
-    rows; columns and values of 120 sampled blocks (seeded) on 3 rows."""
+    configuration bench.py times: the pattern fingerprint (entry count and
+    sum of splitmix64(l M + j) mod 2^64) of every block over every row equals
+    the oracle's; columns and values of 120 sampled blocks (seeded) on 3
+    rows."""
     w = inputs.workload("torus8192g")
     rng = np.random.default_rng(0)
     from oracle.oracle import Oracle
@@ -142,11 +145,11 @@ def test_torus8192_graded_fullsize(td):
     ob = orc.blocks()
     assert [(b[0], b[1]) for b in ob] == asm.blocks()
     nb, M = len(ob), w.M
-    crow = np.sort(rng.choice(M, size=32, replace=False))
-    cnt = orc.pattern_counts(crow, np.arange(nb))
+    hs, nz = orc.pattern_hash(np.arange(nb))
     for b in range(nb):
-        rp = asm.block_csr_torch(b, td.FAR)[0].cpu().numpy()
-        assert np.array_equal(rp[crow + 1] - rp[crow], cnt[b]), "row lengths of block %d" % b
+        rp, col, _ = asm.block_csr_torch(b, td.FAR)
+        h, n = device_fingerprint(rp, col, M)
+        assert n == nz[b] and h == int(hs[b]), "pattern of block %d %s (all rows)" % (b, ob[b][:2])
     rows = np.array([5, 1111, 3333])
     blocks = np.sort(rng.choice(nb, size=120, replace=False))
     res = orc.assemble_rows(rows, blocks)

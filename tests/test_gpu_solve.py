@@ -64,8 +64,10 @@ def test_solve_fp64_matches_dense_lu(td, case, orc):
     asm = td.Assembler(td.Mesh(V, F), td.TimeGrid(t), precision=0)
     asm.assemble()
     g = asm.rhs(0, PLANE)
-    alpha, it, rr = asm.solve(g, restart=50, tol=1e-10)
-    alpha2, it2, rr2 = asm.solve(g, restart=50, tol=1e-10)
+    # tolerance 1e-12: with the measured condition (error / residual ~ 1e2)
+    # the iterate then meets the 1e-8 agreement with the dense LU solution
+    alpha, it, rr = asm.solve(g, restart=50, tol=1e-12, max_iter=6000)
+    alpha2, it2, rr2 = asm.solve(g, restart=50, tol=1e-12, max_iter=6000)
     torch.cuda.synchronize()
     a = alpha.cpu().numpy()
     assert np.array_equal(a, alpha2.cpu().numpy()) and it == it2, "solve is not deterministic"
@@ -73,9 +75,9 @@ def test_solve_fp64_matches_dense_lu(td, case, orc):
     err = np.linalg.norm(a - ref) / np.linalg.norm(ref)
     res = np.linalg.norm(orc.hessenberg_apply(a) - orc.rhs(0, PLANE)) / np.linalg.norm(orc.rhs(0, PLANE))
     print("GMRES(50) fp64: %d iterations, rel res %.3e, vs dense LU %.3e, true residual %.3e" % (it, rr, err, res))
-    assert rr <= 1e-10
-    assert res <= 1e-9
-    assert err <= 1e-6
+    assert rr <= 1e-12
+    assert res <= 1e-11
+    assert err <= 1e-8
 
 
 def test_solve_mixed_converges(td, case):
