@@ -83,6 +83,7 @@ typedef int tdbem_status;
 #define TDBEM_E_DEVICE 6        /* a kernel reported an inconsistency (status word) */
 #define TDBEM_E_NOT_ASSEMBLED 7 /* values requested before an assemble call */
 #define TDBEM_E_UNSUPPORTED 8   /* configuration not supported by this build */
+#define TDBEM_E_NUMERIC 9       /* a host iteration (Schur form of a small Hessenberg matrix) did not converge */
 
 /* Precision of the far field (element pairs without a shared vertex). */
 #define TDBEM_PREC_FP64 0  /* plain: everything in FP64 */
@@ -124,6 +125,9 @@ typedef struct {
     int64_t graph_replays;   /* assemblies replayed from the recorded CUDA graph */
     int64_t matvec_variant;  /* matvec launch shape chosen by the autotuner (-1: not tuned yet) */
     int64_t quad_points_far; /* of quad_points: far element pairs (non-equidistant grids; -1 otherwise) */
+    int64_t matvec_launches; /* kernels one tdbem_hessenberg_apply launches: 3 in the mixed path on an
+                                equidistant grid (padded FP32 copy of x, the blocks outside the Toeplitz
+                                class, the Toeplitz class from per-pair lag windows), else 2 */
 } tdbem_stats_t;
 
 /* Thread-local description of the last failure; never NULL. */
@@ -317,6 +321,45 @@ TDBEM_API tdbem_status tdbem_double_layer(const tdbem_asm *a, const double *alph
 TDBEM_API tdbem_status tdbem_solve_gmres(const tdbem_asm *a, const double *g_dev, double *alpha_dev,
                                          int32_t restart, double tol, int32_t max_iter, int32_t *iters,
                                          double *rel_res, void *stream);
+
+/* Solve A alpha = g by DGMRES(restart, l) (Sec. 4.1): restarted GMRES
+ * right-preconditioned by the deflation preconditioner
+ *   M^-1 = I + U (|lambda_max| T^-1 - I) U^T,  T = U^T A U,
+ * fixed within a cycle. After every cycle that does not converge, the
+ * invariant subspace of the cycle's square Hessenberg matrix H_m (of A M^-1)
+ * for its eigenvalues of modulus at most the l-th smallest (a complex pair
+ * counts twice) is mapped through the Krylov basis, orthonormalised against U
+ * (two Gram-Schmidt passes; a vector with less than 1e-10 of its norm left is
+ * dropped) and appended, until U has r columns; the largest modulus among the
+ * eigenvalues of H_m is the estimate of |lambda_max|. l = 0 or r = 0 is
+ * GMRES(restart). Products, Gram-Schmidt (classical, two passes) and
+ * M^-1 run on the device; the Schur decomposition of H_m, T^-1 and the
+ * small least-squares problem on the host.
+ * g and alpha: caller-owned device arrays of N*M doubles, not overlapping;
+ * zero initial guess; stop when the residual estimate reaches tol ||g|| or a
+ * restart finds the true residual there, or after max_iter iterations.
+ * *iters: iterations done; *rel_res: the true relative residual of the
+ * result; *deflated: columns of U at the end (each may be NULL). Work space:
+ * (restart + 2 + 2 r) N M doubles. Synchronizes the stream.
+ * TDBEM_E_NOT_ASSEMBLED before an assembly; TDBEM_E_INVALID_ARG for restart
+ * outside 1..62, l < 0, r outside 0..62, tol <= 0, max_iter < 1, NULL or
+ * overlapping arrays; TDBEM_E_NUMERIC if the Schur iteration of H_m does not
+ * converge; TDBEM_E_OOM if the work space cannot be allocated. */
+TDBEM_API tdbem_status tdbem_solve_dgmres(const tdbem_asm *a, const double *g_dev, double *alpha_dev,
+                                          int32_t restart, int32_t l, int32_t r, double tol, int32_t max_iter,
+                                          int32_t *iters, double *rel_res, int32_t *deflated, void *stream);
+
+/* Deflation subspace of one DGMRES cycle (host only, no device work): for
+ * the m x m upper Hessenberg matrix H (row-major, row stride ldh; entries
+ * below the subdiagonal are ignored), an orthonormal real basis B of its
+ * invariant subspace for the eigenvalues of modulus at most the l-th
+ * smallest (times 1 + 1e-12), written column k at B[i * m + k], i < m
+ * (B: caller-owned host array of m * m doubles); *sdim: its dimension;
+ * *lam_max: the largest modulus among the eigenvalues. l = 0 returns
+ * only *lam_max. TDBEM_E_INVALID_ARG for m outside 1..62, ldh < m or NULL
+ * arrays; TDBEM_E_NUMERIC if the Schur iteration does not converge. */
+TDBEM_API tdbem_status tdbem_deflation_basis(const double *H, int32_t m, int32_t ldh, int32_t l, double *B,
+                                             int32_t *sdim, double *lam_max);
 
 /* Solve A alpha = g by flexible GMRES FGMRES(restart, levels(inner...)) with
  * the recursive algebraic block-Hessenberg preconditioner (Sec. 4.2,

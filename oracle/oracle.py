@@ -72,6 +72,8 @@ def lib():
                                       np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS"), i64p]
         L.or_assemble_rows.argtypes = [C.c_void_p, i64p, C.c_int64, i64p, C.c_int64, i64p, i32p, f64p, f64p]
         L.or_num_threads.restype = C.c_int
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -102,6 +104,11 @@ def ss_rule(kase, n):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_threads(n):
+    """OpenMP thread count of later oracle calls; returns the previous one."""
+    return lib().or_set_threads(int(n))
 
 
 # ---------------------------------------------------------------- data g --

@@ -1215,3 +1215,17 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Thread count of later parallel regions (n >= 1); returns the previous
+ * count. Only the timing of the oracle uses it (its single-thread rate). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    const int prev = omp_get_max_threads();
+    if (n >= 1) omp_set_num_threads(n);
+    return prev;
+#else
+    (void)n;
+    return 1;
+#endif
+}

@@ -398,6 +398,15 @@ struct tdbem_asm {
     // block-Hessenberg matvec: run descriptors and the transposed-x scratch
     DevBuf mv_blk, mv_xT;
     std::vector<MvBlock> mv_host;
+    // mixed path on an equidistant grid: the Toeplitz class (inner blocks
+    // (k, 1) and (1, 2)) as per-pair lag windows (toeplitz.cu), every other
+    // block by the CSR kernel (mv_rest)
+    bool tw_on = false;
+    int tw_TW = 8, tw_S = 0, tw_PADL = 0;
+    int64_t tw_nfar = 0, tw_nnear = 0;
+    size_t tw_cap_far = 0, tw_cap_near = 0;
+    DevBuf tw_cnt, tw_ptr, tw_tot, tw_fhdr, tw_fval, tw_nhdr, tw_nval, mv_rest;
+    std::vector<MvBlock> mv_rest_host;
     mutable int mv_variant = -1;  // matvec launch shape chosen by the autotuner
     // repeated assemblies: the recorded device sequence (CUDA graph)
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -914,6 +923,18 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     if ((s = dev_alloc(A->ndense_spec, (size_t)NSPEC * M * m.NB * sizeof(double), st))) return bail(s);
     if ((s = dev_alloc(A->status, 16, st))) return bail(s);
     const size_t nb = A->blocks.size();
+    {
+        bool has_c2 = false;
+        for (const Block &b : A->blocks) has_c2 |= b.cls == C2;
+        A->tw_on = !A->fp64 && A->only_k < 0 && has_c2 && tg->N >= 3;
+        if (A->tw_on) {
+            A->tw_TW = tw_lags(A->KW);
+            tw_geometry(A->tw_TW, A->cls_dhi[C2], (int)tg->N, &A->tw_PADL, &A->tw_S);
+            if ((s = dev_alloc(A->tw_cnt, 2 * M * sizeof(int64_t), st))) return bail(s);
+            if ((s = dev_alloc(A->tw_ptr, 2 * (M + 1) * sizeof(int64_t), st))) return bail(s);
+            if ((s = dev_alloc(A->tw_tot, 2 * sizeof(int64_t), st))) return bail(s);
+        }
+    }
     if ((s = dev_alloc(A->cnt_far, nb * M * sizeof(int64_t), st))) return bail(s);
     if ((s = dev_alloc(A->cnt_near, nb * M * sizeof(int64_t), st))) return bail(s);
     if ((s = dev_alloc(A->rp_far, nb * (M + 1) * sizeof(int64_t), st))) return bail(s);
@@ -1010,10 +1031,17 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
         block_run(A.blocks[b].kb, A.blocks[b].ib, N, d.k0, d.i0, d.cnt);
         if (A.graded) d.cnt = 1;  // graded grid: every block stands only for itself
     }
+    A.mv_rest_host.clear();
+    if (A.tw_on)
+        for (size_t b = 0; b < nb; ++b)
+            if (A.blocks[b].cls != C2) A.mv_rest_host.push_back(A.mv_host[b]);
     tdbem_status s;
     if ((s = upload(A.mv_blk, A.mv_host, st))) return s;
-    if (A.mv_xT.n < (size_t)(N * M) * sizeof(double))
-        if ((s = dev_alloc(A.mv_xT, (size_t)(N * M) * sizeof(double), st))) return s;
+    if (A.tw_on && !A.mv_rest_host.empty())
+        if ((s = upload(A.mv_rest, A.mv_rest_host, st))) return s;
+    const size_t xbytes = std::max((size_t)(N * M) * sizeof(double), (size_t)(A.tw_on ? M * A.tw_S : 0) * sizeof(float));
+    if (A.mv_xT.n < xbytes)
+        if ((s = dev_alloc(A.mv_xT, xbytes, st))) return s;
     CUDA_TRY(cudaStreamSynchronize(st));
     return TDBEM_OK;
 }
@@ -1024,6 +1052,46 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
 // the device work only, to be recorded into a CUDA graph; everything the host
 // computed is then known from the eager run (same mesh and time grid give the
 // same tables, pattern and sizes).
+// Per-pair lag windows of the Toeplitz class for the mixed matvec, from the
+// window bounds and the far (FP32 pairs) and near (FP64) windows the assembly
+// has just accumulated. Eager: counts, scan, sizes to the host, buffers
+// grown if needed, fill. capture: the device work with the sizes of the
+// eager run.
+static tdbem_status build_toeplitz(tdbem_asm *A, bool capture, cudaStream_t st) {
+    if (!A->tw_on) return TDBEM_OK;
+    const int64_t M = A->mesh->M, NB = A->mesh->NB;
+    const size_t MM = (size_t)M * M;
+    const int16_t *dlo = (const int16_t *)A->wdlo.p + C2 * MM, *dhi = (const int16_t *)A->wdhi.p + C2 * MM;
+    const int TW = A->tw_TW;
+    launch_tw_count(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, TW, (int64_t *)A->tw_cnt.p,
+                    st);
+    launch_scan_rows((const int64_t *)A->tw_cnt.p, M, 2, (int64_t *)A->tw_ptr.p, (int64_t *)A->tw_tot.p, st);
+    if (!capture) {
+        int64_t tot[2] = {0, 0};
+        CUDA_TRY(cudaMemcpyAsync(tot, A->tw_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        A->tw_nfar = tot[0];
+        A->tw_nnear = tot[1];
+        tdbem_status s;
+        if ((size_t)tot[0] > A->tw_cap_far || !A->tw_fhdr.p) {
+            if ((s = dev_alloc(A->tw_fhdr, std::max<int64_t>(tot[0], 1) * sizeof(int2), st))) return s;
+            if ((s = dev_alloc(A->tw_fval, std::max<int64_t>(tot[0], 1) * TW * sizeof(float), st))) return s;
+            A->tw_cap_far = (size_t)tot[0];
+        }
+        if ((size_t)tot[1] > A->tw_cap_near || !A->tw_nhdr.p) {
+            if ((s = dev_alloc(A->tw_nhdr, std::max<int64_t>(tot[1], 1) * sizeof(int2), st))) return s;
+            if ((s = dev_alloc(A->tw_nval, std::max<int64_t>(tot[1], 1) * TW * sizeof(double), st))) return s;
+            A->tw_cap_near = (size_t)tot[1];
+        }
+    }
+    launch_tw_fill(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, TW,
+                   (const int64_t *)A->tw_ptr.p, (const float2 *)A->dense.p + C2 * MM * A->KW,
+                   (const double *)A->ndense.p + (size_t)C2 * M * NB * A->KW, A->KW, (int)NB, (int2 *)A->tw_fhdr.p,
+                   (float *)A->tw_fval.p, (int2 *)A->tw_nhdr.p, (double *)A->tw_nval.p, st);
+    CUDA_TRY(cudaGetLastError());
+    return TDBEM_OK;
+}
+
 static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     const tdbem_mesh &m = *A->mesh;
     const int64_t M = m.M, E = m.E;
@@ -1198,6 +1266,8 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                     (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true,
                     st);
         CUDA_TRY(cudaGetLastError());
+        tdbem_status ts = build_toeplitz(A, true, st);
+        if (ts) return ts;
         CUDA_TRY(mark(4));
         return TDBEM_OK;
     }
@@ -1239,6 +1309,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                 (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
                 (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
     CUDA_TRY(cudaGetLastError());
+    if ((s = build_toeplitz(A, false, st))) return s;
     CUDA_TRY(mark(4));
     int status = 0;
     CUDA_TRY(cudaMemcpyAsync(&status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1266,7 +1337,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
         // and per colour: far, near (+ far special blocks in the mixed path)
         int64_t ncol = 0;
         for (size_t c = 0; c + 1 < A->color_off.size(); ++c) ncol += A->color_off[c + 1] > A->color_off[c];
-        A->stats.kernel_launches = 12 + ncol * (A->fp64 ? 2 : 3);
+        A->stats.kernel_launches = 12 + ncol * (A->fp64 ? 2 : 3) + (A->tw_on ? 3 : 0);
     }
     if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
     if ((s = plan_matvec(*A, st))) return s;
@@ -1658,6 +1729,38 @@ tdbem_status tdbem_block_csr_host(const tdbem_asm *A, int64_t b, int32_t which, 
 static std::mutex g_mv_mu;
 static std::map<std::vector<int64_t>, int> g_mv_best;
 
+// Kernels of one product: 3 (padded FP32 copy of x, CSR kernel on the
+// blocks outside the Toeplitz class, Toeplitz kernel) where the assembler
+// has the per-pair windows, else 2 (transpose, CSR kernel).
+static int mv_launches(const tdbem_asm *A) { return A->tw_on ? 3 : 2; }
+
+// The whole product y = A x; scratch: the assembler's, or the fixed array of
+// the no-allocation entry point (xbytes usable bytes).
+static cudaError_t mv_launch(const tdbem_asm *A, const double *x, void *scratch, size_t xbytes, double *y, int nsm,
+                             int variant, cudaStream_t st) {
+    const int64_t N = A->tg->N, M = A->mesh->M;
+    if (A->tw_on && (size_t)(M * A->tw_S) * sizeof(float) <= xbytes) {
+        cudaError_t e = launch_hessenberg_rest((const MvBlock *)A->mv_rest.p, (int)A->mv_rest_host.size(), x, y, M,
+                                               (int)N, nsm, variant, st);
+        if (e != cudaSuccess) return e;
+        TwArgs g;
+        g.M = M;
+        g.nin = (int)N - 2;
+        g.TW = A->tw_TW;
+        g.S = A->tw_S;
+        g.PADL = A->tw_PADL;
+        g.fptr = (const int64_t *)A->tw_ptr.p;
+        g.nptr = (const int64_t *)A->tw_ptr.p + (M + 1);
+        g.fhdr = (const int2 *)A->tw_fhdr.p;
+        g.fval = (const float *)A->tw_fval.p;
+        g.nhdr = (const int2 *)A->tw_nhdr.p;
+        g.nval = (const double *)A->tw_nval.p;
+        return launch_toeplitz(g, x, (float *)scratch, y, nsm, st);
+    }
+    return launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, (double *)scratch, y, M,
+                             (int)N, nsm, variant, st);
+}
+
 static tdbem_status tune_matvec(const tdbem_asm *A, const double *x, double *y, int nsm, cudaStream_t st) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -1679,12 +1782,9 @@ static tdbem_status tune_matvec(const tdbem_asm *A, const double *x, double *y, 
     tdbem_status s = TDBEM_OK;
     for (int v = 0; v < MV_NVARIANTS && !s; ++v) {
         float ms = 0.f;
-        cudaError_t e = launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x,
-                                          (double *)A->mv_xT.p, y, M, (int)N, nsm, v, st);
+        cudaError_t e = mv_launch(A, x, A->mv_xT.p, A->mv_xT.n, y, nsm, v, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess)
-            e = launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x,
-                                  (double *)A->mv_xT.p, y, M, (int)N, nsm, v, st);
+        if (e == cudaSuccess) e = mv_launch(A, x, A->mv_xT.p, A->mv_xT.n, y, nsm, v, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -1715,8 +1815,7 @@ tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double 
         tdbem_status ts = tune_matvec(A, x, y, nsm, st);
         if (ts) return ts;
     }
-    CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, (double *)A->mv_xT.p, y,
-                               M, (int)N, nsm, A->mv_variant, st));
+    CUDA_TRY(mv_launch(A, x, A->mv_xT.p, A->mv_xT.n, y, nsm, A->mv_variant, st));
     return TDBEM_OK;
 }
 
@@ -1736,8 +1835,8 @@ tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x,
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     // the shape the autotuner chose for this assembler, if any (no timing here)
-    CUDA_TRY(launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, xT, y, M, (int)N,
-                               nsm, A->mv_variant < 0 ? 0 : A->mv_variant, (cudaStream_t)stream));
+    CUDA_TRY(mv_launch(A, x, xT, (size_t)MV_STATIC_MAX * sizeof(double), y, nsm, A->mv_variant < 0 ? 0 : A->mv_variant,
+                       (cudaStream_t)stream));
     return TDBEM_OK;
 }
 
@@ -1940,6 +2039,250 @@ tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, i
     return TDBEM_OK;
 }
 
+tdbem_status tdbem_deflation_basis(const double *H, int32_t m, int32_t ldh, int32_t l, double *B, int32_t *sdim,
+                                   double *lam_max) {
+    if (!H || !B || !sdim || !lam_max) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (m < 1 || m > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "m must be in 1..62");
+    if (ldh < m) return fail(TDBEM_E_INVALID_ARG, "ldh < m");
+    if (l < 0) return fail(TDBEM_E_INVALID_ARG, "l < 0");
+    int sd = 0;
+    double lm = 0.0;
+    if (deflation_basis(H, m, ldh, l, B, &sd, &lm)) return fail(TDBEM_E_NUMERIC, "Schur iteration did not converge");
+    *sdim = sd;
+    *lam_max = lm;
+    return TDBEM_OK;
+}
+
+// DGMRES(m, l) of Sec. 4.1, the cycle structure of restarted GMRES above with
+// the deflation preconditioner applied to each basis vector before the
+// product and to the correction V y; U and A U live on the device, T^-1 on
+// the host.
+tdbem_status tdbem_solve_dgmres(const tdbem_asm *A, const double *g, double *x, int32_t restart, int32_t l,
+                                int32_t r, double tol, int32_t max_iter, int32_t *iters, double *rel_res,
+                                int32_t *deflated, void *stream) {
+    if (!A || !g || !x) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
+    if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
+    if (restart < 1 || restart > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "restart must be in 1..62");
+    if (l < 0) return fail(TDBEM_E_INVALID_ARG, "l must be >= 0");
+    if (r < 0 || r > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "r must be in 0..62");
+    if (!(tol > 0.0) || max_iter < 1) return fail(TDBEM_E_INVALID_ARG, "need tol > 0 and max_iter >= 1");
+    const int64_t n = A->tg->N * A->mesh->M;
+    const char *gb = (const char *)g, *xb = (const char *)x;
+    if (gb < xb + n * 8 && xb < gb + n * 8) return fail(TDBEM_E_INVALID_ARG, "g and x overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = restart;
+    DevBuf Vb, wb, zb, Ub, AUb, pb, hb, sb;
+    tdbem_status s;
+    if ((s = dev_alloc(Vb, (size_t)(m + 1) * n * sizeof(double), st))) return s;
+    if ((s = dev_alloc(wb, (size_t)n * sizeof(double), st))) return s;
+    if ((s = dev_alloc(zb, (size_t)n * sizeof(double), st))) return s;
+    if (r > 0 && l > 0) {
+        if ((s = dev_alloc(Ub, (size_t)r * n * sizeof(double), st))) return s;
+        if ((s = dev_alloc(AUb, (size_t)r * n * sizeof(double), st))) return s;
+    }
+    if ((s = dev_alloc(pb, (size_t)GM_BLOCKS * GM_MAXV * sizeof(double), st))) return s;
+    if ((s = dev_alloc(hb, (size_t)2 * GM_MAXV * sizeof(double), st))) return s;
+    if ((s = dev_alloc(sb, (size_t)GM_MAXV * sizeof(double), st))) return s;
+    double *V = (double *)Vb.p, *w = (double *)wb.p, *z = (double *)zb.p, *U = (double *)Ub.p,
+           *AU = (double *)AUb.p, *part = (double *)pb.p, *hd = (double *)hb.p, *sd = (double *)sb.p;
+    auto dot = [&](const double *Vv, int nv, const double *ww, double *hout) -> tdbem_status {
+        launch_multi_dot(Vv, n, nv, ww, n, part, hd, st);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaMemcpyAsync(hout, hd, nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return TDBEM_OK;
+    };
+    auto upload = [&](const double *hv, int nv) -> tdbem_status {
+        CUDA_TRY(cudaMemcpyAsync(sd, hv, nv * sizeof(double), cudaMemcpyHostToDevice, st));
+        return TDBEM_OK;
+    };
+    // deflation state: nu columns of U, T^-1 (row-major nu x nu), |lambda_max|
+    int nu = 0;
+    double lam = 1.0;
+    std::vector<double> Tinv;
+    // out = M^-1 v (out != v)
+    auto prec = [&](const double *v, double *out) -> tdbem_status {
+        CUDA_TRY(cudaMemcpyAsync(out, v, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (nu == 0) return TDBEM_OK;
+        std::vector<double> c(nu), d(nu);
+        tdbem_status ps = dot(U, nu, v, c.data());
+        if (ps) return ps;
+        for (int i = 0; i < nu; ++i) {
+            double t = 0.0;
+            for (int k = 0; k < nu; ++k) t += Tinv[(size_t)i * nu + k] * c[k];
+            d[i] = lam * t - c[i];
+        }
+        if ((ps = upload(d.data(), nu))) return ps;
+        launch_multi_axpy(U, n, nu, sd, 1.0, out, n, st);
+        CUDA_TRY(cudaGetLastError());
+        return TDBEM_OK;
+    };
+    CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    double gn2 = 0.0;
+    if ((s = dot(g, 1, g, &gn2))) return s;
+    const double gnorm = sqrt(gn2);
+    int total = 0;
+    double rr = 0.0;
+    if (gnorm == 0.0) {
+        if (iters) *iters = 0;
+        if (rel_res) *rel_res = 0.0;
+        if (deflated) *deflated = 0;
+        return TDBEM_OK;
+    }
+    const double one = 1.0;
+    std::vector<double> H((size_t)(m + 1) * m), Hr((size_t)(m + 1) * m), cs(m), sn(m), e(m + 1), y(m),
+        hv(2 * GM_MAXV), Bm((size_t)m * m);
+    auto true_residual = [&](double &b2) -> tdbem_status {
+        tdbem_status ts = tdbem_hessenberg_apply(A, x, w, stream);
+        if (ts) return ts;
+        CUDA_TRY(cudaMemcpyAsync(V, g, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if ((ts = upload(&one, 1))) return ts;
+        launch_multi_axpy(w, n, 1, sd, -1.0, V, n, st);
+        return dot(V, 1, V, &b2);
+    };
+    for (;;) {
+        double b2 = 0.0;
+        if ((s = true_residual(b2))) return s;
+        const double beta = sqrt(b2);
+        rr = beta / gnorm;
+        if (rr <= tol || total >= max_iter) break;
+        if ((s = upload(&beta, 1))) return s;
+        launch_scale_copy(V, sd, V, n, st);
+        std::fill(e.begin(), e.end(), 0.0);
+        std::fill(Hr.begin(), Hr.end(), 0.0);
+        e[0] = beta;
+        int jdone = 0;
+        bool stop = false;
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (int64_t)j * n, *vn = V + (int64_t)(j + 1) * n;
+            if ((s = prec(vj, z))) return s;
+            if ((s = tdbem_hessenberg_apply(A, z, w, stream))) return s;
+            for (int pass = 0; pass < 2; ++pass) {
+                if ((s = dot(V, j + 1, w, hv.data() + pass * GM_MAXV))) return s;
+                launch_multi_axpy(V, n, j + 1, hd, -1.0, w, n, st);
+            }
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = Hr[(size_t)i * m + j] = hv[i] + hv[GM_MAXV + i];
+            double w2 = 0.0;
+            if ((s = dot(w, 1, w, &w2))) return s;
+            const double hn = sqrt(w2);
+            H[(size_t)(j + 1) * m + j] = Hr[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) {
+                if ((s = upload(&hn, 1))) return s;
+                launch_scale_copy(w, sd, vn, n, st);
+            }
+            for (int i = 0; i < j; ++i) {
+                const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+            }
+            const double a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+            const double rho = hypot(a, b);
+            cs[j] = rho > 0.0 ? a / rho : 1.0;
+            sn[j] = rho > 0.0 ? b / rho : 0.0;
+            H[(size_t)j * m + j] = rho;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            e[j + 1] = -sn[j] * e[j];
+            e[j] = cs[j] * e[j];
+            ++total;
+            jdone = j + 1;
+            rr = fabs(e[j + 1]) / gnorm;
+            if (rr <= tol || total >= max_iter || hn == 0.0) {
+                stop = true;
+                break;
+            }
+        }
+        for (int i = jdone - 1; i >= 0; --i) {
+            double v = e[i];
+            for (int k = i + 1; k < jdone; ++k) v -= H[(size_t)i * m + k] * y[k];
+            y[i] = H[(size_t)i * m + i] != 0.0 ? v / H[(size_t)i * m + i] : 0.0;
+        }
+        // x += M^-1 (V y)
+        CUDA_TRY(cudaMemsetAsync(w, 0, n * sizeof(double), st));
+        if ((s = upload(y.data(), jdone))) return s;
+        launch_multi_axpy(V, n, jdone, sd, -1.0, w, n, st);  // w = -V y
+        if ((s = prec(w, z))) return s;
+        if ((s = upload(&one, 1))) return s;
+        launch_multi_axpy(z, n, 1, sd, -1.0, x, n, st);  // x -= M^-1 (-V y)
+        CUDA_TRY(cudaGetLastError());
+        if (stop) {
+            if ((s = true_residual(b2))) return s;
+            rr = sqrt(b2) / gnorm;
+            break;
+        }
+        if (l == 0 || nu >= r) continue;
+        // deflation: invariant subspace of H_m for its smallest eigenvalues
+        int ns = 0;
+        double lmax = 0.0;
+        if (deflation_basis(Hr.data(), m, m, l, Bm.data(), &ns, &lmax))
+            return fail(TDBEM_E_NUMERIC, "DGMRES: Schur iteration of H_m did not converge");
+        lam = lmax;
+        const int nu0 = nu;
+        std::vector<double> bk(m), cU(std::max(nu + ns, 1));
+        for (int k = 0; k < ns && nu < r; ++k) {
+            // u = V_m B[:, k] into U column nu, then two Gram-Schmidt passes against U
+            double *u = U + (int64_t)nu * n;
+            for (int i = 0; i < m; ++i) bk[i] = -Bm[(size_t)i * m + k];
+            CUDA_TRY(cudaMemsetAsync(u, 0, n * sizeof(double), st));
+            if ((s = upload(bk.data(), m))) return s;
+            launch_multi_axpy(V, n, m, sd, -1.0, u, n, st);
+            double w0 = 0.0;
+            if ((s = dot(u, 1, u, &w0))) return s;
+            for (int pass = 0; pass < 2 && nu > 0; ++pass) {
+                if ((s = dot(U, nu, u, cU.data()))) return s;
+                launch_multi_axpy(U, n, nu, hd, -1.0, u, n, st);
+            }
+            double w1 = 0.0;
+            if ((s = dot(u, 1, u, &w1))) return s;
+            if (!(sqrt(w1) > 1e-10 * sqrt(w0))) continue;
+            const double nrm = sqrt(w1);
+            if ((s = upload(&nrm, 1))) return s;
+            launch_scale_copy(u, sd, u, n, st);
+            ++nu;
+        }
+        if (nu == nu0) continue;
+        // A U for the new columns, then T = U^T A U and its inverse
+        for (int k = nu0; k < nu; ++k)
+            if ((s = tdbem_hessenberg_apply(A, U + (int64_t)k * n, AU + (int64_t)k * n, stream))) return s;
+        std::vector<double> T((size_t)nu * nu), col(nu);
+        for (int k = 0; k < nu; ++k) {
+            if ((s = dot(U, nu, AU + (int64_t)k * n, col.data()))) return s;
+            for (int i = 0; i < nu; ++i) T[(size_t)i * nu + k] = col[i];
+        }
+        // Gauss-Jordan with partial pivoting
+        Tinv.assign((size_t)nu * nu, 0.0);
+        for (int i = 0; i < nu; ++i) Tinv[(size_t)i * nu + i] = 1.0;
+        for (int c = 0; c < nu; ++c) {
+            int p = c;
+            for (int i = c + 1; i < nu; ++i)
+                if (fabs(T[(size_t)i * nu + c]) > fabs(T[(size_t)p * nu + c])) p = i;
+            if (T[(size_t)p * nu + c] == 0.0) return fail(TDBEM_E_NUMERIC, "DGMRES: T = U^T A U is singular");
+            for (int k = 0; k < nu; ++k) {
+                std::swap(T[(size_t)c * nu + k], T[(size_t)p * nu + k]);
+                std::swap(Tinv[(size_t)c * nu + k], Tinv[(size_t)p * nu + k]);
+            }
+            const double piv = T[(size_t)c * nu + c];
+            for (int k = 0; k < nu; ++k) {
+                T[(size_t)c * nu + k] /= piv;
+                Tinv[(size_t)c * nu + k] /= piv;
+            }
+            for (int i = 0; i < nu; ++i) {
+                if (i == c) continue;
+                const double f = T[(size_t)i * nu + c];
+                if (f == 0.0) continue;
+                for (int k = 0; k < nu; ++k) {
+                    T[(size_t)i * nu + k] -= f * T[(size_t)c * nu + k];
+                    Tinv[(size_t)i * nu + k] -= f * Tinv[(size_t)c * nu + k];
+                }
+            }
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (iters) *iters = total;
+    if (rel_res) *rel_res = rr;
+    if (deflated) *deflated = nu;
+    return TDBEM_OK;
+}
+
 // shared checks and set-up of tdbem_solve_fgmres and tdbem_precond_apply:
 // validates the arguments, tunes the product if needed (on x, y), fills the
 // solver plan and allocates its workspace
@@ -2026,6 +2369,7 @@ tdbem_status tdbem_stats(const tdbem_asm *A, tdbem_stats_t *out) {
     if (!A || !out) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     *out = A->stats;
     out->matvec_variant = A->mv_variant;
+    out->matvec_launches = mv_launches(A);
     return TDBEM_OK;
 }
 

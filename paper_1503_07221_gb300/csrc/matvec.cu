@@ -69,14 +69,23 @@ __device__ __forceinline__ AccPair shfl_xor(AccPair v, int o) {
     return AccPair{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
 }
 
+// x value of trial vertex j at time index i: from the transposed copy xT
+// (M, N) of type XT, or (XD) from x itself ((N, M) FP64, row stride M),
+// rounded to XT so that both reads give the same value
+template <typename XT, bool XD>
+__device__ __forceinline__ XT x_at(const void *__restrict__ xs, int64_t j, int64_t i, int N, int64_t M) {
+    if constexpr (XD) return (XT)((const double *)xs)[i * M + j];
+    else return ((const XT *)xs)[j * N + i];
+}
+
 // products and sums of one CSR row of one block for the positions of its run.
 // F32: FP32 products of FP32 values and FP32 x, partial sums of at most 32
 // products in FP32, accumulated as FP32 pairs (two-sum) and added into the
 // FP64 row once; otherwise FP64 products and sums.
-template <typename VT, typename XT, bool F32, int PP>
+template <typename VT, typename XT, bool F32, int PP, bool XD>
 __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                           const VT *__restrict__ val, int64_t l, int k0, int i0, int cnt,
-                                          const XT *__restrict__ xT, int N, double *ys, int lane) {
+                                          const void *__restrict__ xs, int N, int64_t M, double *ys, int lane) {
     typedef typename std::conditional<F32, float, double>::type AT;
     typedef typename std::conditional<F32, AccPair, double>::type ACC;
     const int64_t a = rp[l], e = rp[l + 1];
@@ -98,10 +107,10 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
                 for (int t = 0; t < n; ++t) {
                     const int j = __shfl_sync(0xffffffffu, cj, t);
                     const AT v = __shfl_sync(0xffffffffu, cv, t);
-                    const XT *xr = xT + (int64_t)j * N + i0 + pl;
 #pragma unroll
                     for (int m = 0; m < PP; ++m)
-                        if (pl + 32 * m < cnt) part[m] = fma(v, (AT)xr[32 * m], part[m]);
+                        if (pl + 32 * m < cnt)
+                            part[m] = fma(v, (AT)x_at<XT, XD>(xs, j, i0 + pl + 32 * m, N, M), part[m]);
                 }
 #pragma unroll
                 for (int m = 0; m < PP; ++m) acc_add(acc[m], part[m]);
@@ -118,7 +127,7 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
                 const int64_t c1 = min(e, c0 + 32 * 32);
                 AT part = 0;
                 for (int64_t nz = c0 + lane; nz < c1; nz += 32)
-                    part = fma((AT)val[nz], (AT)xT[(int64_t)col[nz] * N + i0 + p], part);
+                    part = fma((AT)val[nz], (AT)x_at<XT, XD>(xs, col[nz], i0 + p, N, M), part);
                 acc_add(acc, part);
             }
 #pragma unroll
@@ -139,14 +148,17 @@ __device__ __forceinline__ void row_apply(const int64_t *__restrict__ rp, const 
 // is ka = ia = 0, nk = nx = N. Each run is cut to the positions p with both
 // k0 + p and i0 + p inside the ranges. active: if given and zero, the
 // kernel does nothing (a converged solve, see fgmres.cu).
-template <typename VT, bool F32, int PP, int WARPS>
+//
+// XD: x is read directly in its (N, M) layout instead of the transposed copy
+// (the blocks that are not part of a diagonal run: consecutive columns of a
+// CSR row are then consecutive addresses).
+template <typename VT, bool F32, int PP, int WARPS, bool XD>
 __global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *__restrict__ blk, int nb,
-                                                                const void *__restrict__ xT_,
+                                                                const void *__restrict__ xs,
                                                                 double *__restrict__ y, int64_t M, int ka, int nk,
                                                                 int ia, int nx, const int *__restrict__ active) {
     typedef typename std::conditional<F32, float, double>::type XT;
     if (active && !*active) return;
-    const XT *xT = (const XT *)xT_;
     extern __shared__ double ys_all[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *ys = ys_all + (size_t)w * nk;
@@ -159,8 +171,10 @@ __global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *_
             const int phi = min(B.cnt, min(ka + nk - B.k0, ia + nx - B.i0));
             if (phi <= plo) continue;
             const int k0 = B.k0 + plo - ka, i0 = B.i0 + plo - ia, cnt = phi - plo;
-            row_apply<VT, XT, F32, PP>(B.rp_far, B.col_far, (const VT *)B.val_far, l, k0, i0, cnt, xT, nx, ys, lane);
-            row_apply<double, XT, false, PP>(B.rp_near, B.col_near, B.val_near, l, k0, i0, cnt, xT, nx, ys, lane);
+            row_apply<VT, XT, F32, PP, XD>(B.rp_far, B.col_far, (const VT *)B.val_far, l, k0, i0, cnt, xs, nx, M, ys,
+                                           lane);
+            row_apply<double, XT, false, PP, XD>(B.rp_near, B.col_near, B.val_near, l, k0, i0, cnt, xs, nx, M, ys,
+                                                 lane);
         }
         for (int k = lane; k < nk; k += 32) y[(int64_t)k * M + l] = ys[k];
         __syncwarp();
@@ -170,17 +184,31 @@ __global__ void __launch_bounds__(WARPS * 32) hessenberg_kernel(const MvBlock *_
 // The tunable launch shapes: (positions per lane, warps per CTA).
 static const int MV_VARIANTS[MV_NVARIANTS][2] = {{4, 8}, {2, 8}, {8, 8}, {4, 4}, {2, 4}, {8, 4}};
 
-template <typename VT, bool F32, int PP, int WARPS>
+template <typename VT, bool F32, int PP, int WARPS, bool XD = false>
 static cudaError_t launch_mv_shape(const MvBlock *blk, int nb, const void *xT, double *y, int64_t M, int ka, int nk,
                                    int ia, int nx, const int *active, int nsm, cudaStream_t st) {
     const size_t smem = (size_t)WARPS * nk * sizeof(double);
     const int64_t ctas = (M + WARPS - 1) / WARPS;
     const int grid = (int)std::min<int64_t>(ctas, (int64_t)nsm * 16);
-    cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32, PP, WARPS>,
+    cudaError_t e = cudaFuncSetAttribute(hessenberg_kernel<VT, F32, PP, WARPS, XD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    hessenberg_kernel<VT, F32, PP, WARPS><<<grid, WARPS * 32, smem, st>>>(blk, nb, xT, y, M, ka, nk, ia, nx, active);
+    hessenberg_kernel<VT, F32, PP, WARPS, XD>
+        <<<grid, WARPS * 32, smem, st>>>(blk, nb, xT, y, M, ka, nk, ia, nx, active);
     return cudaGetLastError();
+}
+
+// the blocks outside the Toeplitz class in the mixed path, x read directly
+cudaError_t launch_hessenberg_rest(const MvBlock *blk, int nb, const double *x, double *y, int64_t M, int N, int nsm,
+                                   int variant, cudaStream_t st) {
+    switch (variant) {
+        case 1: return launch_mv_shape<float, true, 2, 8, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+        case 2: return launch_mv_shape<float, true, 8, 8, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+        case 3: return launch_mv_shape<float, true, 4, 4, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+        case 4: return launch_mv_shape<float, true, 2, 4, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+        case 5: return launch_mv_shape<float, true, 8, 4, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+        default: return launch_mv_shape<float, true, 4, 8, true>(blk, nb, x, y, M, 0, N, 0, N, nullptr, nsm, st);
+    }
 }
 
 template <typename VT, bool F32>

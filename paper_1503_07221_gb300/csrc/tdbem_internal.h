@@ -234,6 +234,35 @@ struct MvBlock {
     const double *val_near;
     int32_t k0, i0, cnt, pad;
 };
+// the blocks outside the Toeplitz class in the mixed path (no diagonal runs),
+// x read in its (N, M) layout; writes every entry of y
+cudaError_t launch_hessenberg_rest(const MvBlock *blk, int nb, const double *x, double *y, int64_t M, int N, int nsm,
+                                   int variant, cudaStream_t st);
+
+// toeplitz.cu: the Toeplitz class (inner blocks (k, 1) and (1, 2)) of the
+// mixed path from per-pair lag windows of TW lags, added into y
+struct TwArgs {
+    int64_t M;
+    int nin;                   // inner time indices N - 2
+    int TW, S, PADL;           // lags per entry; row stride and left padding of xP (floats)
+    const int64_t *fptr;       // far entries of row l: [fptr[l], fptr[l + 1])
+    const int2 *fhdr;          // (trial vertex j, first lag)
+    const float *fval;         // TW FP32 values per entry
+    const int64_t *nptr;       // near entries, FP64 values
+    const int2 *nhdr;
+    const double *nval;
+};
+int tw_lags(int KW);
+void tw_geometry(int TW, int max_lag, int N, int *PADL, int *S);
+void launch_tw_count(int64_t M, const int16_t *dlo, const int16_t *dhi, const int64_t *nbr_ptr, const int32_t *nbr,
+                     int TW, int64_t *cnt, cudaStream_t st);
+void launch_tw_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const int64_t *nbr_ptr, const int32_t *nbr,
+                    int TW, const int64_t *ptr, const float2 *dense, const double *ndense, int KW, int NB, int2 *fhdr,
+                    float *fval, int2 *nhdr, double *nval, cudaStream_t st);
+// transposes x into the padded FP32 copy xP (M x S floats), then adds the
+// Toeplitz class into y
+cudaError_t launch_toeplitz(const TwArgs &g, const double *x, float *xP, double *y, int nsm, cudaStream_t st);
+
 // transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
 // variant: one of MV_NVARIANTS launch shapes (0 = default), see matvec.cu
 constexpr int MV_NVARIANTS = 6;
@@ -258,6 +287,10 @@ void launch_multi_dot(const double *V, int64_t ld, int nv, const double *w, int6
 void launch_multi_axpy(const double *V, int64_t ld, int nv, const double *h, double sign, double *w, int64_t n,
                        cudaStream_t st, const int *active = nullptr);
 void launch_scale_copy(const double *w, const double *beta, double *v, int64_t n, cudaStream_t st);
+// deflation.cu: basis B (m x m row-major, first *sdim columns) of the
+// invariant subspace of the Hessenberg H for its l eigenvalues of smallest
+// modulus, *lam_max the largest modulus; 0, or -1 if the QR iteration fails
+int deflation_basis(const double *H, int m, int ldh, int l, double *B, int *sdim, double *lam_max);
 constexpr int GM_BLOCKS = 256;   // blocks of the dot-product partial sums
 constexpr int GM_MAXV = 64;      // most vectors in one multi_dot / multi_axpy
 

@@ -14,7 +14,8 @@ oracle consume as input data:
 * graded_grid(steps, q, T)   -- dt_n = dt_0*q**n, n = 0..steps-1, summing to T
 
 The named workloads (sphere 320 / 5120 jittered / 20480, torus 8192 graded)
-are assembled by `workload(name)`.
+are assembled by `workload(name)`, the potential evaluations (points on a
+plane, grid times) by `potential_workload(name)`.
 """
 from __future__ import annotations
 
@@ -206,6 +207,48 @@ def workload(name: str) -> Workload:
     if name == "sphere5120p":
         V, F = icosphere(4)
         return Workload(name, V, F, equidistant_grid(65, 4.48), True)
+    raise KeyError(name)
+
+
+@dataclasses.dataclass
+class PotentialWorkload:
+    """Evaluation of the retarded double layer potential off the surface: a
+    mesh and time grid (the density lives on them), points X (P, 3), times
+    (nt,) and the Gauss points per direction n of the collapsed rule."""
+    name: str
+    verts: np.ndarray
+    tris: np.ndarray
+    t: np.ndarray
+    X: np.ndarray
+    times: np.ndarray
+    n: int
+
+
+def plane_points(side: int, half: float, z: float) -> np.ndarray:
+    """side x side grid of points on [-half, half]^2 at height z, x fastest."""
+    g = np.linspace(-half, half, side)
+    yy, xx = np.meshgrid(g, g, indexing="ij")
+    return np.stack([xx.ravel(), yy.ravel(), np.full(side * side, z)], axis=1)
+
+
+def potential_workload(name: str) -> PotentialWorkload:
+    """Named potential evaluations.
+
+    plane66049_sphere320 : 257 x 257 = 66049 points on the plane z = 0.05
+                           over [-3, 3]^2 (it cuts the sphere), the 40 grid
+                           times t_1..t_40 of N = 41 points on [0, 6], the
+                           320-triangle icosphere, 4 x 4 Gauss points per
+                           triangle
+    plane4096_sphere5120 : 64 x 64 points on the same plane, the same times,
+                           the 5120-triangle icosphere, 4 x 4 points
+    """
+    t = equidistant_grid(41, 6.0)
+    if name == "plane66049_sphere320":
+        V, F = icosphere(2)
+        return PotentialWorkload(name, V, F, t, plane_points(257, 3.0, 0.05), t[1:].copy(), 4)
+    if name == "plane4096_sphere5120":
+        V, F = icosphere(4)
+        return PotentialWorkload(name, V, F, t, plane_points(64, 3.0, 0.05), t[1:].copy(), 4)
     raise KeyError(name)
 
 

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libtdbem.so")
 
 OK = 0
 RHS_PLANE_WAVE, RHS_SPHERE_N0, RHS_SPHERE_N1 = 0, 1, 2
-E_INVALID_ARG, E_MESH, E_TIMEGRID, E_OOM, E_CUDA, E_DEVICE, E_NOT_ASSEMBLED, E_UNSUPPORTED = range(1, 9)
+E_INVALID_ARG, E_MESH, E_TIMEGRID, E_OOM, E_CUDA, E_DEVICE, E_NOT_ASSEMBLED, E_UNSUPPORTED, E_NUMERIC = range(1, 10)
 LAST_BLOCK = -1
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -41,7 +41,8 @@ class Stats(C.Structure):
                 ("far_pairs", C.c_int64), ("near_pairs", C.c_int64), ("quad_points", C.c_int64),
                 ("ms_total", C.c_double), ("ms_pattern", C.c_double), ("ms_far", C.c_double),
                 ("ms_near", C.c_double), ("ms_extract", C.c_double), ("kernel_launches", C.c_int64),
-                ("graph_replays", C.c_int64), ("matvec_variant", C.c_int64), ("quad_points_far", C.c_int64)]
+                ("graph_replays", C.c_int64), ("matvec_variant", C.c_int64), ("quad_points_far", C.c_int64),
+                ("matvec_launches", C.c_int64)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -76,6 +77,9 @@ def lib():
     L.tdbem_double_layer.argtypes = [vp, vp, vp, i64, vp, i32, i32, vp, vp]
     L.tdbem_psi_table.argtypes = [vp, i64, i32, vp, i64, vp, vp]
     L.tdbem_solve_gmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, C.POINTER(i32), C.POINTER(C.c_double), vp]
+    L.tdbem_solve_dgmres.argtypes = [vp, vp, vp, i32, i32, i32, C.c_double, i32, C.POINTER(i32),
+                                     C.POINTER(C.c_double), C.POINTER(i32), vp]
+    L.tdbem_deflation_basis.argtypes = [vp, i32, i32, i32, vp, C.POINTER(i32), C.POINTER(C.c_double)]
     L.tdbem_solve_fgmres.argtypes = [vp, vp, vp, i32, C.c_double, i32, i32, vp, C.POINTER(i32),
                                      C.POINTER(C.c_double), vp]
     L.tdbem_precond_apply.argtypes = [vp, i32, vp, C.c_double, vp, vp, vp]
@@ -133,6 +137,21 @@ def _stream(stream):
         import torch
         return torch.cuda.current_stream().cuda_stream
     return int(stream)
+
+
+def deflation_basis(H, l):
+    """Host-only (no device): (B, lam_max) for the square upper Hessenberg H
+    (m x m, m <= 62): B (m, sdim) an orthonormal real basis of the invariant
+    subspace of H for its eigenvalues of modulus at most the l-th smallest,
+    lam_max the largest eigenvalue modulus (tdbem_deflation_basis)."""
+    import numpy as np
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    m = H.shape[0]
+    B = np.zeros((m, m))
+    sd, lm = C.c_int32(), C.c_double()
+    _check(lib().tdbem_deflation_basis(C.c_void_p(H.ctypes.data), m, m, int(l), C.c_void_p(B.ctypes.data),
+                                       C.byref(sd), C.byref(lm)))
+    return B[:, :sd.value].copy(), lm.value
 
 
 def measure_fma_peaks(stream=None):
@@ -307,6 +326,18 @@ class Assembler:
         _check(lib().tdbem_solve_gmres(self.h, C.c_void_p(g.data_ptr()), C.c_void_p(alpha.data_ptr()), restart, tol,
                                        max_iter, C.byref(it), C.byref(rr), C.c_void_p(_stream(stream))))
         return alpha, it.value, rr.value
+
+    def solve_dgmres(self, g, restart=30, l=5, r=40, tol=1e-8, max_iter=2000, stream=None):
+        """alpha with A alpha = g by DGMRES(restart, l) with at most r
+        deflation vectors (Sec. 4.1); returns (alpha, iterations, true
+        relative residual, columns of U at the end)."""
+        import torch
+        alpha = torch.empty_like(g)
+        it, rr, nu = C.c_int32(), C.c_double(), C.c_int32()
+        _check(lib().tdbem_solve_dgmres(self.h, C.c_void_p(g.data_ptr()), C.c_void_p(alpha.data_ptr()), restart, l, r,
+                                        tol, max_iter, C.byref(it), C.byref(rr), C.byref(nu),
+                                        C.c_void_p(_stream(stream))))
+        return alpha, it.value, rr.value, nu.value
 
     def solve_fgmres(self, g, restart=50, tol=1e-5, max_iter=20000, inner=(10,), stream=None):
         """alpha with A alpha = g by FGMRES(restart, len(inner)(inner...)) with

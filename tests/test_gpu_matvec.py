@@ -49,6 +49,9 @@ def _run(td, V, F, t, precision, rows=None, seed=0):
     assert np.array_equal(y1, y2), "matvec is not deterministic"
     # the first product ran the autotuner; every launch shape sums in the same order
     assert 0 <= asm.stats()["matvec_variant"] < 6
+    # the mixed path applies the Toeplitz class from per-pair lag windows
+    # (three kernels per product), the FP64 path the per-block CSR (two)
+    assert asm.stats()["matvec_launches"] == (3 if precision == 1 else 2)
     orc = Oracle(V, F, t, psi_mode="interp")
     rows = np.arange(M) if rows is None else np.asarray(rows)
     ref = orc.hessenberg_apply(x, rows=rows)
@@ -77,6 +80,18 @@ def test_matvec_sphere20480_sampled(td):
     rows = np.sort(np.random.default_rng(1).choice(w.M, size=3, replace=False))
     rel, ab = _run(td, w.verts, w.tris, w.t, 1, rows=rows)
     print("sphere20480 prec 1 rows %s: max rel %.3e, abs %.3e" % (rows, rel, ab))
+    assert rel < 1e-6 and ab < 1e-6
+
+
+def test_matvec_two_output_chunks(td):
+    # 5120 triangles, N = 140 (138 inner time indices: two chunks of 128
+    # outputs per row in the Toeplitz kernel), lag windows of 9 lags (12 per
+    # entry); sampled rows against the oracle
+    V, F = inputs.icosphere(4)
+    t = inputs.equidistant_grid(140, 139 * 0.05)
+    rows = np.sort(np.random.default_rng(2).choice(V.shape[0], size=3, replace=False))
+    rel, ab = _run(td, V, F, t, 1, rows=rows)
+    print("sphere5120 N=140 prec 1 rows %s: max rel %.3e, abs %.3e" % (rows, rel, ab))
     assert rel < 1e-6 and ab < 1e-6
 
 
