@@ -402,7 +402,7 @@ struct tdbem_asm {
     // (k, 1) and (1, 2)) as per-pair lag windows (toeplitz.cu), every other
     // block by the CSR kernel (mv_rest)
     bool tw_on = false;
-    int tw_TW = 8, tw_S = 0, tw_PADL = 0;
+    int tw_TL = 8, tw_S = 0, tw_PADL = 0;
     int64_t tw_nfar = 0, tw_nnear = 0;
     size_t tw_cap_far = 0, tw_cap_near = 0;
     DevBuf tw_cnt, tw_ptr, tw_tot, tw_fhdr, tw_fval, tw_nhdr, tw_nval, mv_rest;
@@ -928,11 +928,9 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
         for (const Block &b : A->blocks) has_c2 |= b.cls == C2;
         A->tw_on = !A->fp64 && A->only_k < 0 && has_c2 && tg->N >= 3;
         if (A->tw_on) {
-            A->tw_TW = tw_lags(A->KW);
-            tw_geometry(A->tw_TW, A->cls_dhi[C2], (int)tg->N, &A->tw_PADL, &A->tw_S);
             if ((s = dev_alloc(A->tw_cnt, 2 * M * sizeof(int64_t), st))) return bail(s);
             if ((s = dev_alloc(A->tw_ptr, 2 * (M + 1) * sizeof(int64_t), st))) return bail(s);
-            if ((s = dev_alloc(A->tw_tot, 2 * sizeof(int64_t), st))) return bail(s);
+            if ((s = dev_alloc(A->tw_tot, 4 * sizeof(int64_t), st))) return bail(s);
         }
     }
     if ((s = dev_alloc(A->cnt_far, nb * M * sizeof(int64_t), st))) return bail(s);
@@ -1039,7 +1037,7 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
     if ((s = upload(A.mv_blk, A.mv_host, st))) return s;
     if (A.tw_on && !A.mv_rest_host.empty())
         if ((s = upload(A.mv_rest, A.mv_rest_host, st))) return s;
-    const size_t xbytes = std::max((size_t)(N * M) * sizeof(double), (size_t)(A.tw_on ? M * A.tw_S : 0) * sizeof(float));
+    const size_t xbytes = std::max((size_t)(N * M) * sizeof(double), (size_t)(A.tw_on ? 4 * M * A.tw_S : 0) * sizeof(float));
     if (A.mv_xT.n < xbytes)
         if ((s = dev_alloc(A.mv_xT, xbytes, st))) return s;
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1054,7 +1052,8 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
 // same tables, pattern and sizes).
 // Per-pair lag windows of the Toeplitz class for the mixed matvec, from the
 // window bounds and the far (FP32 pairs) and near (FP64) windows the assembly
-// has just accumulated. Eager: counts, scan, sizes to the host, buffers
+// has just accumulated. Eager: counts, scan, sizes and the widest window to
+// the host (which fix the lags per entry and the x-copy geometry), buffers
 // grown if needed, fill. capture: the device work with the sizes of the
 // eager run.
 static tdbem_status build_toeplitz(tdbem_asm *A, bool capture, cudaStream_t st) {
@@ -1062,29 +1061,35 @@ static tdbem_status build_toeplitz(tdbem_asm *A, bool capture, cudaStream_t st) 
     const int64_t M = A->mesh->M, NB = A->mesh->NB;
     const size_t MM = (size_t)M * M;
     const int16_t *dlo = (const int16_t *)A->wdlo.p + C2 * MM, *dhi = (const int16_t *)A->wdhi.p + C2 * MM;
-    const int TW = A->tw_TW;
-    launch_tw_count(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, TW, (int64_t *)A->tw_cnt.p,
-                    st);
-    launch_scan_rows((const int64_t *)A->tw_cnt.p, M, 2, (int64_t *)A->tw_ptr.p, (int64_t *)A->tw_tot.p, st);
+    int64_t *tot = (int64_t *)A->tw_tot.p;
+    CUDA_TRY(cudaMemsetAsync(tot + 2, 0, sizeof(int64_t), st));
+    launch_tw_count(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, (int64_t *)A->tw_cnt.p,
+                    (unsigned long long *)(tot + 2), st);
+    launch_scan_rows((const int64_t *)A->tw_cnt.p, M, 2, (int64_t *)A->tw_ptr.p, tot, st);
     if (!capture) {
-        int64_t tot[2] = {0, 0};
-        CUDA_TRY(cudaMemcpyAsync(tot, A->tw_tot.p, sizeof(tot), cudaMemcpyDeviceToHost, st));
+        int64_t h[3] = {0, 0, 0};
+        CUDA_TRY(cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        A->tw_nfar = tot[0];
-        A->tw_nnear = tot[1];
+        A->tw_nfar = h[0];
+        A->tw_nnear = h[1];
+        const int TL = tw_lags((int)std::max<int64_t>(h[2], 1));
+        if (TL < 0) return fail(TDBEM_E_DEVICE, "Toeplitz-class lag window wider than 16 lags");
+        A->tw_TL = TL;
+        tw_geometry(TL, A->cls_dhi[C2], (int)A->tg->N, &A->tw_PADL, &A->tw_S);
+        const int TS = (TL + 3) / 4 * 4;
         tdbem_status s;
-        if ((size_t)tot[0] > A->tw_cap_far || !A->tw_fhdr.p) {
-            if ((s = dev_alloc(A->tw_fhdr, std::max<int64_t>(tot[0], 1) * sizeof(int2), st))) return s;
-            if ((s = dev_alloc(A->tw_fval, std::max<int64_t>(tot[0], 1) * TW * sizeof(float), st))) return s;
-            A->tw_cap_far = (size_t)tot[0];
+        if ((size_t)h[0] * TS > A->tw_cap_far || !A->tw_fhdr.p) {
+            if ((s = dev_alloc(A->tw_fhdr, std::max<int64_t>(h[0], 1) * sizeof(int2), st))) return s;
+            if ((s = dev_alloc(A->tw_fval, std::max<int64_t>(h[0], 1) * TS * sizeof(float), st))) return s;
+            A->tw_cap_far = (size_t)h[0] * TS;
         }
-        if ((size_t)tot[1] > A->tw_cap_near || !A->tw_nhdr.p) {
-            if ((s = dev_alloc(A->tw_nhdr, std::max<int64_t>(tot[1], 1) * sizeof(int2), st))) return s;
-            if ((s = dev_alloc(A->tw_nval, std::max<int64_t>(tot[1], 1) * TW * sizeof(double), st))) return s;
-            A->tw_cap_near = (size_t)tot[1];
+        if ((size_t)h[1] * TS > A->tw_cap_near || !A->tw_nhdr.p) {
+            if ((s = dev_alloc(A->tw_nhdr, std::max<int64_t>(h[1], 1) * sizeof(int2), st))) return s;
+            if ((s = dev_alloc(A->tw_nval, std::max<int64_t>(h[1], 1) * TS * sizeof(double), st))) return s;
+            A->tw_cap_near = (size_t)h[1] * TS;
         }
     }
-    launch_tw_fill(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, TW,
+    launch_tw_fill(M, dlo, dhi, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p, A->tw_TL,
                    (const int64_t *)A->tw_ptr.p, (const float2 *)A->dense.p + C2 * MM * A->KW,
                    (const double *)A->ndense.p + (size_t)C2 * M * NB * A->KW, A->KW, (int)NB, (int2 *)A->tw_fhdr.p,
                    (float *)A->tw_fval.p, (int2 *)A->tw_nhdr.p, (double *)A->tw_nval.p, st);
@@ -1739,14 +1744,15 @@ static int mv_launches(const tdbem_asm *A) { return A->tw_on ? 3 : 2; }
 static cudaError_t mv_launch(const tdbem_asm *A, const double *x, void *scratch, size_t xbytes, double *y, int nsm,
                              int variant, cudaStream_t st) {
     const int64_t N = A->tg->N, M = A->mesh->M;
-    if (A->tw_on && (size_t)(M * A->tw_S) * sizeof(float) <= xbytes) {
+    if (A->tw_on && (size_t)(4 * M * A->tw_S) * sizeof(float) <= xbytes) {
+        // variants: 3 Toeplitz shapes (outputs per lane) x 2 CSR shapes
         cudaError_t e = launch_hessenberg_rest((const MvBlock *)A->mv_rest.p, (int)A->mv_rest_host.size(), x, y, M,
-                                               (int)N, nsm, variant, st);
+                                               (int)N, nsm, variant < 3 ? 0 : 3, st);
         if (e != cudaSuccess) return e;
         TwArgs g;
         g.M = M;
         g.nin = (int)N - 2;
-        g.TW = A->tw_TW;
+        g.TL = A->tw_TL;
         g.S = A->tw_S;
         g.PADL = A->tw_PADL;
         g.fptr = (const int64_t *)A->tw_ptr.p;
@@ -1755,7 +1761,7 @@ static cudaError_t mv_launch(const tdbem_asm *A, const double *x, void *scratch,
         g.fval = (const float *)A->tw_fval.p;
         g.nhdr = (const int2 *)A->tw_nhdr.p;
         g.nval = (const double *)A->tw_nval.p;
-        return launch_toeplitz(g, x, (float *)scratch, y, nsm, st);
+        return launch_toeplitz(g, x, (float *)scratch, y, tw_variant_outputs(variant), nsm, st);
     }
     return launch_hessenberg((const MvBlock *)A->mv_blk.p, (int)A->blocks.size(), A->fp64, x, (double *)scratch, y, M,
                              (int)N, nsm, variant, st);

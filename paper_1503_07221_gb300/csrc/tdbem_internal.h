@@ -240,28 +240,31 @@ cudaError_t launch_hessenberg_rest(const MvBlock *blk, int nb, const double *x, 
                                    int variant, cudaStream_t st);
 
 // toeplitz.cu: the Toeplitz class (inner blocks (k, 1) and (1, 2)) of the
-// mixed path from per-pair lag windows of TW lags, added into y
+// mixed path from per-pair lag windows of TL lags, added into y
 struct TwArgs {
     int64_t M;
     int nin;                   // inner time indices N - 2
-    int TW, S, PADL;           // lags per entry; row stride and left padding of xP (floats)
+    int TL, S, PADL;           // lags per entry; row stride and left padding of the x copies (floats)
     const int64_t *fptr;       // far entries of row l: [fptr[l], fptr[l + 1])
     const int2 *fhdr;          // (trial vertex j, first lag)
-    const float *fval;         // TW FP32 values per entry
+    const float *fval;         // TL FP32 values per entry, stride TL rounded up to 4
     const int64_t *nptr;       // near entries, FP64 values
     const int2 *nhdr;
     const double *nval;
 };
-int tw_lags(int KW);
-void tw_geometry(int TW, int max_lag, int N, int *PADL, int *S);
+// lags per entry for the widest window (8, 9, 10, 12 or 16; -1 above 16)
+int tw_lags(int maxw);
+// outputs per lane of a matvec variant (the autotuner's index)
+int tw_variant_outputs(int variant);
+void tw_geometry(int TL, int max_lag, int N, int *PADL, int *S);
 void launch_tw_count(int64_t M, const int16_t *dlo, const int16_t *dhi, const int64_t *nbr_ptr, const int32_t *nbr,
-                     int TW, int64_t *cnt, cudaStream_t st);
+                     int64_t *cnt, unsigned long long *maxw, cudaStream_t st);
 void launch_tw_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const int64_t *nbr_ptr, const int32_t *nbr,
-                    int TW, const int64_t *ptr, const float2 *dense, const double *ndense, int KW, int NB, int2 *fhdr,
+                    int TL, const int64_t *ptr, const float2 *dense, const double *ndense, int KW, int NB, int2 *fhdr,
                     float *fval, int2 *nhdr, double *nval, cudaStream_t st);
-// transposes x into the padded FP32 copy xP (M x S floats), then adds the
-// Toeplitz class into y
-cudaError_t launch_toeplitz(const TwArgs &g, const double *x, float *xP, double *y, int nsm, cudaStream_t st);
+// writes the four shifted FP32 copies of x (4 x M x S floats at xP), then
+// adds the Toeplitz class into y with R outputs per lane (4, 8 or 16)
+cudaError_t launch_toeplitz(const TwArgs &g, const double *x, float *xP, double *y, int R, int nsm, cudaStream_t st);
 
 // transposes x (N, M) into xT (M, N), then y = A x; returns the launch status
 // variant: one of MV_NVARIANTS launch shapes (0 = default), see matvec.cu
