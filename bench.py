@@ -198,6 +198,13 @@ def job_throughput(units_per_rank, world, ms):
     return units_per_rank * world / (ms * 1e-3)
 
 
+# DRAM bytes (read + written) of one far phase, all colour launches of one
+# assembly, from one single-pass ncu capture of the current far kernel on
+# that workload (summary under profiles/); None where no capture exists.
+# An entry goes when the kernel changes.
+FAR_TRAFFIC = {"sphere20480": 202.30e9 + 132.86e9}
+
+
 def far_flops(st):
     # algorithmic FP32 work of the far kernel per far point pair: distance
     # and Chebyshev argument (~14 FMA-equivalents), T_n recurrence (31 FMA),
@@ -368,7 +375,8 @@ def measure_assembly(name, precision, steps, warmup, matvecs, *, world=1, rank=0
         "assembly_only_nnz_per_s": nnz * world / (float(np.mean(asm_ms)) * 1e-3),
         "matvec_nnz_reuse_per_s": mv_work * world / (mv_ms * 1e-3) if matvecs else None,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak32, "unit": "TFLOP/s",
-                     "frac": achieved / peak32, "traffic": None,
+                     "frac": achieved / peak32, "traffic": None if graded else FAR_TRAFFIC.get(name),
+                     "traffic_unit": "bytes per far phase (all colour launches of one assembly)",
                      "kernel": ("gfar_kernel<false>" if graded else "far32_kernel") + " (FP32 FMA pipe)",
                      "peak_basis": "measured: packed FP32 FMA microbenchmark (tdbem_measure_fma_peaks) "
                                    "after the timed region",
