@@ -1242,7 +1242,8 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
         na.rule_w64 = (const double *)A->rule_w64.p; na.rule_l64 = (const double *)A->rule_l64.p;
         const int grid = (int)std::min<int64_t>(na.ncolor, (int64_t)2 * nsm);
         if (grid > 0) {
-            launch_near(na, grid, st);
+            if (A->fp64) launch_near(na, grid, st);
+            else launch_near32(na, A->c32, grid, st);
             // mixed: the far pairs of the special blocks, FP64 (the FP32 kernel skips them)
             if (!A->fp64) launch_farspec(na, (int)std::min<int64_t>(na.ncolor, (int64_t)8 * nsm), st);
         }

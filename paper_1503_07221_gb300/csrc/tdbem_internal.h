@@ -220,6 +220,8 @@ struct NearArgs {
     int *status;
 };
 void launch_near(const NearArgs &a, int grid, cudaStream_t st);
+// near32.cu: the same near field with psi, psi~ in FP32 (mixed path)
+void launch_near32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st);
 // far element pairs that reach a special block, FP64 7-point rule
 void launch_farspec(const NearArgs &a, int grid, cudaStream_t st);
 
