@@ -447,6 +447,88 @@ struct tdbem_asm {
 
 static int kind_of(int64_t i, int64_t N) { return i == 0 ? 0 : (i == N - 1 ? 2 : 1); }  // F, I, L
 
+// Rebalanced copy of the mesh's vertex-disjoint triangle colouring for the
+// equidistant far and near kernels, which take one colour per launch with G
+// CTAs, each a whole test triangle at a time: a colour of n triangles costs
+// about ceil(n / G) rounds. Triangles move from a colour's last partial round
+// into colours with room in theirs wherever none of their vertices is used
+// there (the colouring stays vertex-disjoint), until no colour's excess can
+// move; empty colours are dropped. Deterministic: colours and triangles are
+// taken in a fixed order.
+static std::vector<std::vector<int32_t>> balance_colours(const tdbem_mesh &m, int G) {
+    const int ncol = (int)m.colors.size();
+    std::vector<std::vector<int32_t>> out = m.colors;
+    if (ncol < 2 || ncol > 64 || G < 1) return out;
+    const int32_t *F = m.F.data();
+    std::vector<uint64_t> vmask(m.M, 0);
+    std::vector<int> col(m.E, -1);
+    std::vector<int64_t> size(ncol, 0);
+    for (int c = 0; c < ncol; ++c)
+        for (int32_t t : m.colors[c]) {
+            col[t] = c;
+            ++size[c];
+            for (int k = 0; k < 3; ++k) vmask[F[3 * t + k]] |= 1ull << c;
+        }
+    auto rounds = [&]() {
+        int64_t w = 0;
+        for (int c = 0; c < ncol; ++c) w += (size[c] + G - 1) / G;
+        return w;
+    };
+    for (int it = 0; it < 4 * ncol + 64; ++it) {
+        const int64_t w0 = rounds();
+        std::vector<int> order(ncol);
+        std::iota(order.begin(), order.end(), 0);
+        auto excess = [&](int c) { return size[c] % G ? size[c] % G : (int64_t)G; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return excess(a) < excess(b); });
+        bool improved = false;
+        for (int c : order) {
+            const int64_t ex = size[c] % G;
+            if (ex == 0) continue;
+            std::vector<int> tg;
+            for (int d = 0; d < ncol; ++d)
+                if (d != c && size[d] % G != 0) tg.push_back(d);
+            std::stable_sort(tg.begin(), tg.end(), [&](int a, int b) { return size[a] % G > size[b] % G; });
+            int64_t moved = 0;
+            for (int64_t t = 0; t < m.E && moved < ex; ++t) {
+                if (col[t] != c) continue;
+                const uint64_t used = vmask[F[3 * t]] | vmask[F[3 * t + 1]] | vmask[F[3 * t + 2]];
+                for (int d : tg) {
+                    if (size[d] % G == 0 || ((used >> d) & 1ull)) continue;
+                    for (int k = 0; k < 3; ++k) vmask[F[3 * t + k]] = (vmask[F[3 * t + k]] & ~(1ull << c)) | (1ull << d);
+                    col[t] = d;
+                    --size[c];
+                    ++size[d];
+                    ++moved;
+                    break;
+                }
+            }
+            if (moved == ex || rounds() < w0) {
+                improved = true;
+                break;
+            }
+        }
+        if (!improved) break;
+    }
+    out.assign(ncol, {});
+    for (int64_t t = 0; t < m.E; ++t) out[col[t]].push_back((int32_t)t);
+    out.erase(std::remove_if(out.begin(), out.end(), [](const std::vector<int32_t> &v) { return v.empty(); }),
+              out.end());
+    // every colour vertex-disjoint, every triangle once: else keep the mesh's colouring
+    std::vector<int> stamp(m.M, -1);
+    int64_t total = 0;
+    for (size_t c = 0; c < out.size(); ++c) {
+        total += (int64_t)out[c].size();
+        for (int32_t t : out[c])
+            for (int k = 0; k < 3; ++k) {
+                int &st = stamp[F[3 * t + k]];
+                if (st == (int)c) return m.colors;
+                st = (int)c;
+            }
+    }
+    if (total != m.E) return m.colors;
+    return out;
+}
+
 static tdbem_status plan_blocks(tdbem_asm &A) {
     const tdbem_timegrid &tg = *A.tg;
     const int64_t N = tg.N;
@@ -823,10 +905,19 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     if (!A->fp64 && far32_smem(far32_window(mesh->max_dq, dt), A->KW, mesh->max_nv) > 227 * 1024)
         return bail(fail(TDBEM_E_UNSUPPORTED, "mixed precision: far-kernel shared memory exceeds 227 KB"));
     const tdbem_mesh &m = *mesh;
-    // uploads
+    // uploads; the colouring rebalanced for the far kernel's grid on this device
+    int nsm_dev = 0;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm_dev, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return bail(fail(TDBEM_E_CUDA, std::string("device attributes: ") + cudaGetErrorString(e)));
+    }
+    const int far_grid = (A->fp64 || far32_window(m.max_dq, dt) > 2) ? nsm_dev : 2 * nsm_dev;
+    const std::vector<std::vector<int32_t>> bal = balance_colours(m, far_grid);
     std::vector<int32_t> colors;
     A->color_off.assign(1, 0);
-    for (auto &c : m.colors) { colors.insert(colors.end(), c.begin(), c.end()); A->color_off.push_back((int64_t)colors.size()); }
+    for (auto &c : bal) { colors.insert(colors.end(), c.begin(), c.end()); A->color_off.push_back((int64_t)colors.size()); }
     std::vector<float> rw(7), rl(21);
     for (int k = 0; k < 7; ++k) { rw[k] = (float)m.rule_W[k]; for (int d = 0; d < 3; ++d) rl[3 * k + d] = (float)m.rule_L[k][d]; }
 #define UP(buf, vec) if ((s = upload(A->buf, vec, st))) return bail(s)
