@@ -134,16 +134,48 @@ __device__ static void decide(const LagTables &lt, double dmin, double dmax, Pai
     r.smask = sm;
 }
 
-// One thread per element pair. The bounds are first computed in FP32; the
-// lag decisions are taken at both ends of a band of +-tol2 around the FP32
-// squared distances (tol2 covers the FP32 rounding of the squared distances
-// with a wide margin) and, only when the two ends disagree, the pair is
-// recomputed exactly in FP64. The decisions are therefore those of the FP64
-// computation.
-__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // trial
-    const int64_t q = blockIdx.y;                                       // test
-    if (s >= g.E) return;
+// The decisions of `decide` in FP32: thr holds, per class c from off[c],
+// the thresholds b_d - tie (n_c of them) then a_d + tie, rounded to FP32.
+__device__ static void decide32(const float *thr, const int *off, const LagTables &lt, float dmin, float dmax,
+                                PairRec &r) {
+    for (int c = 0; c < NLAG; ++c) {
+        r.lo[c] = 0; r.cnt[c] = 0;
+        const int n = lt.dhi[c] - lt.dlo[c] + 1;
+        if (n <= 0) continue;
+        const float *tb = thr + off[c], *ta = tb + n;
+        int L = 0, H = n;  // first index with tb > dmin
+        while (L < H) {
+            const int m = (L + H) >> 1;
+            if (tb[m] > dmin) H = m; else L = m + 1;
+        }
+        const int lo = L;
+        L = -1; H = n - 1;  // last index with ta < dmax
+        while (L < H) {
+            const int m = (L + H + 1) >> 1;
+            if (ta[m] < dmax) L = m; else H = m - 1;
+        }
+        const int hi = L;
+        if (lo <= hi) { r.lo[c] = (int16_t)(lt.dlo[c] + lo); r.cnt[c] = (uint8_t)(hi - lo + 1); }
+    }
+    uint8_t sm = 0;
+    for (int c = NLAG; c < NCLASS; ++c) {
+        if (lt.dlo[c] > lt.dhi[c]) continue;
+        if (dmin < thr[off[c]] && dmax > thr[off[c] + 1]) sm |= (uint8_t)(1u << (c - NLAG));
+    }
+    r.smask = sm;
+}
+
+// One thread per element pair. The bounds are first computed in FP32, and
+// the lag decisions are taken in FP32 at both ends of a band around them:
+// the squared distances +-2 tol2 (tol2 covers their FP32 rounding with a
+// wide margin, the second tol2 the rounding of the band ends and square
+// roots), widened by 2^-20 max(T, d) for the FP32 rounding of the
+// thresholds. Where both ends give the same decisions, no threshold lies
+// between them and the exact FP64 distance decides the same; only where they
+// differ is the pair recomputed exactly in FP64 and decided in FP64. The
+// decisions are therefore those of the FP64 computation.
+__device__ static void pair_bounds_one(const Geo &g, const LagTables &lt, PairRec *rec, int64_t q, int64_t s,
+                                       const float *pb_thr, const int *pb_off, float tmax) {
     const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
     int shared = 0;
     for (int i = 0; i < 3; ++i)
@@ -157,9 +189,13 @@ __global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
     float mn2, mx2;
     tri_bounds2<f3, float>(a, b, shared != 0, mn2, mx2);
     PairRec r0, r1;
-    const double t2 = lt.tol2;
-    decide(lt, shared ? 0.0 : sqrt(fmax((double)mn2 - t2, 0.0)), sqrt(fmax((double)mx2 - t2, 0.0)), r0);
-    decide(lt, shared ? 0.0 : sqrt((double)mn2 + t2), sqrt((double)mx2 + t2), r1);
+    const float t2 = 2.0f * (float)lt.tol2;
+    const float hx = sqrtf(mx2 + t2);
+    const float mg = 9.5367431640625e-07f * fmaxf(tmax, hx);  // 2^-20 max(|threshold|, d)
+    const float lx = sqrtf(fmaxf(mx2 - t2, 0.f)) - mg;
+    const float ln = shared ? 0.f : sqrtf(fmaxf(mn2 - t2, 0.f)) - mg, hn = shared ? 0.f : sqrtf(mn2 + t2) + mg;
+    decide32(pb_thr, pb_off, lt, ln, lx, r0);
+    decide32(pb_thr, pb_off, lt, hn, hx + mg, r1);
     bool same = r0.smask == r1.smask;
     for (int c = 0; c < NLAG; ++c) same = same && r0.lo[c] == r1.lo[c] && r0.cnt[c] == r1.cnt[c];
     PairRec r = r0;
@@ -175,9 +211,44 @@ __global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
     rec[q * g.E + s] = r;
 }
 
+// One CTA per test triangle q, its threads over the trial triangles.
+__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
+    extern __shared__ float pb_thr[];
+    __shared__ int pb_off[NCLASS + 1];
+    __shared__ float pb_tmax;
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int c = 0; c < NCLASS; ++c) {
+            pb_off[c] = o;
+            o += 2 * max(lt.dhi[c] - lt.dlo[c] + 1, 0);
+        }
+        pb_off[NCLASS] = o;
+    }
+    __syncthreads();
+    for (int c = 0; c < NCLASS; ++c) {
+        const int n = max(lt.dhi[c] - lt.dlo[c] + 1, 0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            pb_thr[pb_off[c] + i] = (float)(lt.b[c][i] - lt.tie);
+            pb_thr[pb_off[c] + n + i] = (float)(lt.a[c][i] + lt.tie);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < pb_off[NCLASS]; ++i) t = fmaxf(t, fabsf(pb_thr[i]));
+        pb_tmax = t;
+    }
+    __syncthreads();
+    const int64_t q = blockIdx.x;  // test
+    for (int64_t s = threadIdx.x; s < g.E; s += blockDim.x)  // trial
+        pair_bounds_one(g, lt, rec, q, s, pb_thr, pb_off, pb_tmax);
+}
+
+
 void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st) {
-    dim3 grid((unsigned)((g.E + 127) / 128), (unsigned)g.E);
-    pair_bounds_kernel<<<grid, 128, 0, st>>>(g, lt, rec);
+    int nthr = 0;
+    for (int c = 0; c < NCLASS; ++c) nthr += 2 * std::max(lt.dhi[c] - lt.dlo[c] + 1, 0);
+    pair_bounds_kernel<<<(unsigned)g.E, 256, (size_t)nthr * sizeof(float), st>>>(g, lt, rec);
 }
 
 // Graded grids: exact FP64 bounds (dmin, dmax) of every element pair (dmin
