@@ -16,7 +16,8 @@
  *
  * with continuous piecewise-linear hat functions phi on a flat triangle
  * mesh and the C-infinity partition-of-unity time basis b of Sec. 3
- * (Eq. BasisFunctions, p = 0). Row = test (k, l), column = trial (i, j);
+ * (Eq. BasisFunctions; p = 0, or p = 1, 2 with the Legendre factors of
+ * b_{i,m}, m = 0..p). Row = test (k, l), column = trial (i, j);
  * every block is spatially symmetric, so this is also the paper's A_{k,i}(j,l).
  *
  * Blocks (Sec. 3.2): A is block Hessenberg (Eq. Apartitioned); block (k,i)
@@ -148,7 +149,16 @@ TDBEM_API tdbem_status tdbem_mesh_create(const double *verts_xyz, int64_t M, con
                                int64_t E, tdbem_mesh **out);
 
 /* Time grid of N points (host): t[0] = 0 < t[1] < ... < t[N-1] = T (Sec. 3).
- * p: Legendre degree of the time basis (only 0 in this build); basis_kind:
+ * p: Legendre degree of the time basis, 0, 1 or 2 (else TDBEM_E_UNSUPPORTED):
+ * the L = N (p + 1) time functions b_{k,m} of Eq. BasisFunctions, numbered
+ * k (p + 1) + m (Sec. 3), the Legendre coordinate mapping each function's
+ * support onto [-1, 1] (on a non-equidistant grid, the support of the inner
+ * function i is [t_{i-1}, t_{i+1}]). With p >= 1 every nonzero block and
+ * order pair (k, i, m2, m1) is assembled from its own psi on any grid (the
+ * path of non-equidistant grids: no Toeplitz reuse), at most 256 blocks
+ * times orders in one block column; the block-Hessenberg preconditioner,
+ * tdbem_assemble_block, tdbem_psi_table and tdbem_double_layer take p = 0
+ * only (TDBEM_E_UNSUPPORTED). basis_kind:
  * the smooth step that builds the partition of unity, TDBEM_STEP_ERF_ARTANH
  * (0) = the paper's f = erf(2 artanh x)/2 + 1/2, TDBEM_STEP_EXP_INV (1) =
  * F(s) = h(s)/(h(s) + h(1-s)), h(s) = exp(-1/s), s = (x+1)/2 (any other
@@ -223,13 +233,13 @@ TDBEM_API tdbem_status tdbem_block_csr_host(const tdbem_asm *a, int64_t b, int32
 /* y = A x for the whole block-Hessenberg space-time matrix (Sec. 5.1, Eq.
  * Apartitioned), every block taken from the unique blocks of the last
  * assembly through Eq. relationAtildeBlock; blocks cut by the diam criterion
- * are zero. x and y are caller-owned device arrays of N*M doubles, block row
- * k at [k*M, k*M + M) (time index k of the trial / test basis function,
- * vertex index within); they must not overlap. FP64 mode: products and sums
- * in FP64. MIXED mode: x rounded to FP32, FP32 products of the FP32 far
- * values summed in FP32 over at most 32 products, partial sums and near
- * terms accumulated in FP64. Asynchronous on
- * `stream`; uses a scratch buffer owned by the assembler (N*M doubles,
+ * are zero. x and y are caller-owned device arrays of L*M doubles (L = N (p
+ * + 1) time functions), row k (p + 1) + m at [(k (p + 1) + m) M, ... + M)
+ * (time function b_{k,m} of the trial / test side, vertex index within);
+ * they must not overlap. FP64 mode: products and sums in FP64. MIXED mode:
+ * x rounded to FP32, FP32 products of the FP32 far values, FP32 partial sums
+ * accumulated as FP32 pairs, near terms in FP64. Asynchronous on
+ * `stream`; uses a scratch buffer owned by the assembler (L*M doubles,
  * allocated by tdbem_assemble_all), so calls on one assembler must be
  * ordered on one stream. TDBEM_E_NOT_ASSEMBLED before an assembly,
  * TDBEM_E_INVALID_ARG for NULL or overlapping x / y, TDBEM_E_CUDA if the
@@ -243,7 +253,7 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply(const tdbem_asm *a, const double *
  * device memory to its own pool, or code under a fixed memory budget where
  * an allocation failing halfway through a run is not acceptable. The
  * transposed x goes to a fixed scratch array of 2^21 doubles (16 MiB) in
- * device global memory; N*M above 2^21 is rejected with TDBEM_E_INVALID_ARG
+ * device global memory; L*M above 2^21 is rejected with TDBEM_E_INVALID_ARG
  * before anything runs. The runtime reserves that array when it loads the
  * library's module on a device, which it does lazily at the first call of
  * this entry point there: a caller that commits all remaining device memory
@@ -259,8 +269,9 @@ TDBEM_API tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *a, const 
 
 /* Right-hand side of the linear system (Sec. 3): g_k(l) = int_0^T int_Gamma
  * g(x,t) phi_l(x) bdot_k(t) dGamma dt for every time basis function k and
- * vertex l, written to the caller-owned device array g_dev of N*M doubles
- * (row k at [k*M, k*M + M)). FP64; 7-point rule on every triangle, composite
+ * vertex l, for p >= 1 with bdot_{k,m} of every order m, written to the
+ * caller-owned device array g_dev of L*M doubles (row k (p + 1) + m at
+ * [(k (p + 1) + m) M, ... + M)). FP64; 7-point rule on every triangle, composite
  * Gauss-Legendre in time split at every grid point. Neumann data g by kind:
  *   TDBEM_RHS_PLANE_WAVE: sound-hard scattering of u_inc = exp(-(t - x.d -
  *     c0)^2 / (2 w^2)); params = {dx, dy, dz, c0, w} (nparams 5, d is
@@ -310,7 +321,7 @@ TDBEM_API tdbem_status tdbem_double_layer(const tdbem_asm *a, const double *alph
 /* Solve A alpha = g (the block-Hessenberg system of Eq. Apartitioned) by
  * restarted GMRES(restart) (Sec. 4) with tdbem_hessenberg_apply as the
  * product: zero initial guess, stop when ||g - A alpha|| <= tol ||g|| or after
- * max_iter iterations. g and alpha are caller-owned device arrays of N*M
+ * max_iter iterations. g and alpha are caller-owned device arrays of L*M
  * doubles that must not overlap; the Krylov basis ((restart+1) N M doubles)
  * is allocated through the registered allocator for the call and freed
  * before it returns. On return *iters holds the iterations done and *rel_res
@@ -335,7 +346,7 @@ TDBEM_API tdbem_status tdbem_solve_gmres(const tdbem_asm *a, const double *g_dev
  * GMRES(restart). Products, Gram-Schmidt (classical, two passes) and
  * M^-1 run on the device; the Schur decomposition of H_m, T^-1 and the
  * small least-squares problem on the host.
- * g and alpha: caller-owned device arrays of N*M doubles, not overlapping;
+ * g and alpha: caller-owned device arrays of L*M doubles, not overlapping;
  * zero initial guess; stop when the residual estimate reaches tol ||g|| or a
  * restart finds the true residual there, or after max_iter iterations.
  * *iters: iterations done; *rel_res: the true relative residual of the
@@ -373,7 +384,7 @@ TDBEM_API tdbem_status tdbem_deflation_basis(const double *H, int32_t m, int32_t
  * splitting of that half while l < levels and the half spans two blocks or
  * more; the last level is unpreconditioned. levels = 0 runs the same
  * iteration without a preconditioner (GMRES(restart)).
- * g and alpha: caller-owned device arrays of N*M doubles, not overlapping;
+ * g and alpha: caller-owned device arrays of L*M doubles, not overlapping;
  * zero initial guess; stop when the residual estimate reaches tol ||g||, or
  * when a restart finds the true residual there, or after max_iter outer
  * iterations. *iters: outer iterations done; *rel_res: the true relative

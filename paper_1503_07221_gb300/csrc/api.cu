@@ -368,6 +368,7 @@ struct tdbem_timegrid {
 struct Block {
     int kb, ib, cls, lag;
     double a, b;
+    int m2 = 0, m1 = 0;  // temporal orders of the test and trial functions (p >= 1)
 };
 
 struct tdbem_asm {
@@ -421,13 +422,14 @@ struct tdbem_asm {
     std::vector<GPan64> g_pan64;
     std::vector<float4> g_pan32;
     int g_npan = 0, g_nset64 = 0, g_maxpan = 0, g_njob32 = 0;
+    int g_ncol = 0;  // block columns: one per trial function (i, m1)
     double g_smax = -1.0;  // window spread Dmax - Dmin the batches were planned for
     std::vector<int> g_bi0, g_bi1;           // batches of trial columns [i0, i1)
     std::vector<int64_t> g_doff, g_ndoff;    // per column: window offsets inside its batch
     size_t g_dense_max = 0, g_ndense_max = 0;
     DevBuf gpair, gvmin, gvmax, gpartial, g_ga_d, g_gb_d, g_colblk_d, g_colk0_d, g_cb2api_d, g_pan0_d, g_pan64_d,
         g_pan32_d, g_p64_d, g_kw_d, g_doff_d, g_ndoff_d, g_tkb, g_tib, g_tr0, g_tdr, g_samples, g_coef, g_coef32,
-        g_geol, g_cenh, g_cenl, g_coloff_d, g_dense, g_ndense;
+        g_geol, g_cenh, g_cenl, g_coloff_d, g_dense, g_ndense, g_tm2, g_tm1;
     std::vector<cudaEvent_t> g_ev;
     // one block on its own (tdbem_assemble_block): the planner keeps only
     // block (only_k, only_i); `single` is the sub-assembler of the last call
@@ -444,6 +446,9 @@ struct tdbem_asm {
             if (e) cudaEventDestroy(e);
     }
 };
+
+// rows of x and y: the L = N (p + 1) time functions (Sec. 3 numbering)
+static int64_t time_rows(const tdbem_asm *A) { return A->tg->N * (A->tg->p + 1); }
 
 static int kind_of(int64_t i, int64_t N) { return i == 0 ? 0 : (i == N - 1 ? 2 : 1); }  // F, I, L
 
@@ -606,24 +611,35 @@ static tdbem_status plan_blocks(tdbem_asm &A) {
 // a, b in {0, 1, 2} (Sec. 3.1), which bound its Chebyshev panels.
 static tdbem_status plan_graded(tdbem_asm &A) {
     const tdbem_timegrid &tg = *A.tg;
-    const int64_t N = tg.N;
+    const int64_t N = tg.N, P1 = tg.p + 1;
     const double *t = tg.t.data();
     const double T = t[N - 1];
     const double tie = 1e-12 * T;
     auto tl = [&](int64_t q) { return q == 0 ? 0.0 : t[q - 1]; };
     auto tr = [&](int64_t q) { return q == N - 1 ? T : t[q + 1]; };
     A.blocks.clear();
-    std::vector<int> api_of((size_t)(N * N), -1);
+    // block (k, i) of every order pair (m2, m1): api_of[((k N + i) P1 + m2) P1 + m1]
+    std::vector<int> api_of((size_t)(N * N * P1 * P1), -1);
+    auto aidx = [&](int64_t k, int64_t i, int64_t m2, int64_t m1) { return (size_t)(((k * N + i) * P1 + m2) * P1 + m1); };
     for (int64_t k = 0; k < N; ++k)
         for (int64_t i = 0; i < N && i <= k + 1; ++i) {
             const double a = std::max(0.0, tl(k) - tr(i)), b = tr(k) - tl(i);
             if (!(b > a) || a >= A.mesh->diam - tie) continue;
             if (A.only_k >= 0 && (k != A.only_k || i != A.only_i)) continue;
-            api_of[k * N + i] = (int)A.blocks.size();
-            A.blocks.push_back({(int)k, (int)i, -1, 0, a, b});
+            for (int64_t m2 = 0; m2 < P1; ++m2)
+                for (int64_t m1 = 0; m1 < P1; ++m1) {
+                    api_of[aidx(k, i, m2, m1)] = (int)A.blocks.size();
+                    Block B{(int)k, (int)i, -1, 0, a, b};
+                    B.m2 = (int)m2;
+                    B.m1 = (int)m1;
+                    A.blocks.push_back(B);
+                }
         }
-    A.g_colblk.assign(N + 1, 0);
-    A.g_colk0.assign(N, 0);
+    // columns: one per trial function (i, m1), column index i P1 + m1; the
+    // blocks of a column in order of (k, m2) (a and b do not decrease)
+    A.g_ncol = (int)(N * P1);
+    A.g_colblk.assign(A.g_ncol + 1, 0);
+    A.g_colk0.assign(A.g_ncol, 0);
     A.g_cb2api.clear();
     A.g_ga.clear();
     A.g_gb.clear();
@@ -631,45 +647,49 @@ static tdbem_status plan_graded(tdbem_asm &A) {
     A.g_pan64.clear();
     A.g_pan32.clear();
     A.g_maxpan = 0;
-    for (int64_t i = 0; i < N; ++i) {
-        A.g_colblk[i] = (int)A.g_cb2api.size();
-        int64_t kfirst = -1, klast = -2;
-        for (int64_t k = 0; k < N; ++k)
-            if (api_of[k * N + i] >= 0) {
-                if (kfirst < 0) kfirst = k;
-                else if (k != klast + 1) return fail(TDBEM_E_UNSUPPORTED, "non-contiguous block column");
-                klast = k;
-            }
-        A.g_colk0[i] = kfirst < 0 ? 0 : (int)kfirst;
-        if (klast - kfirst + 1 > GP_MAXK) return fail(TDBEM_E_UNSUPPORTED, "more than 256 blocks in one block column");
-        const int pcol0 = (int)A.g_pan64.size();
-        for (int64_t k = kfirst; kfirst >= 0 && k <= klast; ++k) {
-            const Block &B = A.blocks[api_of[k * N + i]];
-            A.g_cb2api.push_back(api_of[k * N + i]);
-            A.g_ga.push_back(B.a);
-            A.g_gb.push_back(B.b);
-            A.g_pan0.push_back((int)A.g_pan64.size());
-            const double X[3] = {tl(k), t[k], tr(k)}, Y[3] = {tl(i), t[i], tr(i)};
-            std::vector<double> br = {B.a, B.b};
-            for (double x : X)
-                for (double y : Y)
-                    if (x - y > B.a && x - y < B.b) br.push_back(x - y);
-            std::sort(br.begin(), br.end());
-            std::vector<double> m = {br[0]};
-            for (size_t q = 1; q < br.size(); ++q)
-                if (br[q] - m.back() > 1e-13 * T) m.push_back(br[q]);
-            if (m.back() != B.b) m.back() = B.b;
-            if (m.size() < 2 || m.size() - 1 > (size_t)GP_MAXPAN) return fail(TDBEM_E_UNSUPPORTED, "bad panel count");
-            for (size_t q = 0; q + 1 < m.size(); ++q) {
-                const double s = m[q], w = m[q + 1] - m[q], mid = s + 0.5 * w;
-                A.g_pan64.push_back({s, w, 0.0, 0.0});
-                const float mh = (float)mid;
-                A.g_pan32.push_back(make_float4((float)s, mh, (float)(mid - (double)mh), (float)(2.0 / w)));
-            }
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t m1 = 0; m1 < P1; ++m1) {
+            const int64_t col = i * P1 + m1;
+            A.g_colblk[col] = (int)A.g_cb2api.size();
+            int64_t kfirst = -1, klast = -2;
+            for (int64_t k = 0; k < N; ++k)
+                if (api_of[aidx(k, i, 0, m1)] >= 0) {
+                    if (kfirst < 0) kfirst = k;
+                    else if (k != klast + 1) return fail(TDBEM_E_UNSUPPORTED, "non-contiguous block column");
+                    klast = k;
+                }
+            A.g_colk0[col] = kfirst < 0 ? 0 : (int)(kfirst * P1);
+            if ((klast - kfirst + 1) * P1 > GP_MAXK)
+                return fail(TDBEM_E_UNSUPPORTED, "more than 256 blocks (times orders) in one block column");
+            const int pcol0 = (int)A.g_pan64.size();
+            for (int64_t k = kfirst; kfirst >= 0 && k <= klast; ++k)
+                for (int64_t m2 = 0; m2 < P1; ++m2) {
+                    const Block &B = A.blocks[api_of[aidx(k, i, m2, m1)]];
+                    A.g_cb2api.push_back(api_of[aidx(k, i, m2, m1)]);
+                    A.g_ga.push_back(B.a);
+                    A.g_gb.push_back(B.b);
+                    A.g_pan0.push_back((int)A.g_pan64.size());
+                    const double X[3] = {tl(k), t[k], tr(k)}, Y[3] = {tl(i), t[i], tr(i)};
+                    std::vector<double> br = {B.a, B.b};
+                    for (double x : X)
+                        for (double y : Y)
+                            if (x - y > B.a && x - y < B.b) br.push_back(x - y);
+                    std::sort(br.begin(), br.end());
+                    std::vector<double> m = {br[0]};
+                    for (size_t q = 1; q < br.size(); ++q)
+                        if (br[q] - m.back() > 1e-13 * T) m.push_back(br[q]);
+                    if (m.back() != B.b) m.back() = B.b;
+                    if (m.size() < 2 || m.size() - 1 > (size_t)GP_MAXPAN) return fail(TDBEM_E_UNSUPPORTED, "bad panel count");
+                    for (size_t q = 0; q + 1 < m.size(); ++q) {
+                        const double s0 = m[q], w = m[q + 1] - m[q], mid = s0 + 0.5 * w;
+                        A.g_pan64.push_back({s0, w, 0.0, 0.0});
+                        const float mh = (float)mid;
+                        A.g_pan32.push_back(make_float4((float)s0, mh, (float)(mid - (double)mh), (float)(2.0 / w)));
+                    }
+                }
+            A.g_maxpan = std::max(A.g_maxpan, (int)A.g_pan64.size() - pcol0);
         }
-        A.g_maxpan = std::max(A.g_maxpan, (int)A.g_pan64.size() - pcol0);
-    }
-    A.g_colblk[N] = (int)A.g_cb2api.size();
+    A.g_colblk[A.g_ncol] = (int)A.g_cb2api.size();
     A.g_pan0.push_back((int)A.g_pan64.size());
     A.g_npan = (int)A.g_pan64.size();
     // FP64 coefficient sets: S64 sub-panels per panel; the mixed path needs them
@@ -725,7 +745,7 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
     std::vector<double> gx, gw;
     gauss_legendre01(24, gx, gw);
     // psi table jobs: FP32 set (one per panel, mixed path), then the FP64 sets
-    std::vector<int> kb, ib;
+    std::vector<int> kb, ib, tm2, tm1;
     std::vector<double> r0, dr;
     const int ncb = (int)A.g_cb2api.size();
     auto add_jobs = [&](bool fp64set) {
@@ -733,11 +753,17 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
             const Block &B = A.blocks[A.g_cb2api[cb]];
             for (int p = A.g_pan0[cb]; p < A.g_pan0[cb + 1]; ++p) {
                 const GPan64 &q = A.g_pan64[p];
-                if (!fp64set) { kb.push_back(B.kb); ib.push_back(B.ib); r0.push_back(q.x); dr.push_back(q.y); continue; }
+                if (!fp64set) {
+                    kb.push_back(B.kb); ib.push_back(B.ib); tm2.push_back(B.m2); tm1.push_back(B.m1);
+                    r0.push_back(q.x); dr.push_back(q.y);
+                    continue;
+                }
                 if (A.g_p64[p] < 0) continue;
                 for (int sb = 0; sb < A.S64; ++sb) {
                     kb.push_back(B.kb);
                     ib.push_back(B.ib);
+                    tm2.push_back(B.m2);
+                    tm1.push_back(B.m1);
                     r0.push_back(q.x + q.y * sb / A.S64);
                     dr.push_back(q.y / A.S64);
                 }
@@ -757,7 +783,7 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
     UPG(g_coloff_d, A.color_off); UPG(g_ga_d, A.g_ga); UPG(g_gb_d, A.g_gb); UPG(g_colblk_d, A.g_colblk);
     UPG(g_colk0_d, A.g_colk0); UPG(g_cb2api_d, A.g_cb2api); UPG(g_pan0_d, A.g_pan0); UPG(g_pan64_d, A.g_pan64);
     UPG(g_pan32_d, A.g_pan32); UPG(g_p64_d, A.g_p64); UPG(g_tkb, kb); UPG(g_tib, ib); UPG(g_tr0, r0);
-    UPG(g_tdr, dr);
+    UPG(g_tdr, dr); UPG(g_tm2, tm2); UPG(g_tm1, tm1);
     for (int k = 1; k <= 3; ++k) {
         std::vector<double> r = sauter_schwab(k, A.opts.near_order);
         A.ss_npp[k] = (int)(r.size() / 5);
@@ -837,7 +863,7 @@ tdbem_status tdbem_timegrid_create(const double *t, int64_t N, int32_t p, int32_
     if (t[0] != 0.0) return fail(TDBEM_E_TIMEGRID, "t[0] must be 0");
     for (int64_t i = 1; i < N; ++i)
         if (!(t[i] > t[i - 1]) || !std::isfinite(t[i])) return fail(TDBEM_E_TIMEGRID, "t must be finite and strictly increasing");
-    if (p != 0) return fail(TDBEM_E_UNSUPPORTED, "this build takes temporal degree p = 0");
+    if (p < 0 || p > 2) return fail(TDBEM_E_UNSUPPORTED, "this build takes temporal degree p = 0, 1 or 2");
     if (kind != 0 && kind != 1) return fail(TDBEM_E_INVALID_ARG, "basis_kind must be 0 (erf(2 artanh)) or 1 (exp(-1/s))");
     if (!(c > 0.0) || !std::isfinite(c)) return fail(TDBEM_E_INVALID_ARG, "wave speed must be positive");
     tdbem_timegrid *g = new tdbem_timegrid();
@@ -883,7 +909,9 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     A->opts = o;
     A->fp64 = o.precision == TDBEM_PREC_FP64;
     auto bail = [&](tdbem_status s) { delete A; return s; };
-    if (!tg->equidistant) {
+    // non-equidistant grids, and p >= 1 on any grid: every nonzero block
+    // (and order pair) assembled from its own psi
+    if (!tg->equidistant || tg->p > 0) {
         tdbem_status gs = create_graded(*A, st);
         if (gs) return bail(gs);
         *out = A;
@@ -1056,8 +1084,8 @@ tdbem_status tdbem_block_info(const tdbem_asm *a, int64_t b, int32_t *k, int32_t
     if (b < 0 || b >= (int64_t)a->blocks.size()) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
     if (k) *k = a->blocks[b].kb;
     if (i) *i = a->blocks[b].ib;
-    if (m2) *m2 = 0;
-    if (m1) *m1 = 0;
+    if (m2) *m2 = a->blocks[b].m2;
+    if (m1) *m1 = a->blocks[b].m1;
     if (nf) *nf = a->nnz_far[b];
     if (nn) *nn = a->nnz_near[b];
     return TDBEM_OK;
@@ -1106,7 +1134,7 @@ static void block_run(int64_t k, int64_t i, int64_t N, int32_t &k0, int32_t &i0,
 }
 
 static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
-    const int64_t N = A.tg->N, M = A.mesh->M;
+    const int64_t N = A.tg->N, M = A.mesh->M, P1 = A.tg->p + 1, L = N * P1;
     const size_t nb = A.blocks.size();
     A.mv_host.assign(nb, MvBlock{});
     for (size_t b = 0; b < nb; ++b) {
@@ -1118,7 +1146,13 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
         d.col_near = (const int32_t *)A.col_near.p + A.off_near[b];
         d.val_near = (const double *)A.val_near.p + A.off_near[b];
         block_run(A.blocks[b].kb, A.blocks[b].ib, N, d.k0, d.i0, d.cnt);
-        if (A.graded) d.cnt = 1;  // graded grid: every block stands only for itself
+        if (A.graded) {
+            // every block stands only for itself, at row k (p + 1) + m2 and
+            // column i (p + 1) + m1 of the time functions
+            d.k0 = (int32_t)(A.blocks[b].kb * P1 + A.blocks[b].m2);
+            d.i0 = (int32_t)(A.blocks[b].ib * P1 + A.blocks[b].m1);
+            d.cnt = 1;
+        }
     }
     A.mv_rest_host.clear();
     if (A.tw_on)
@@ -1128,7 +1162,7 @@ static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
     if ((s = upload(A.mv_blk, A.mv_host, st))) return s;
     if (A.tw_on && !A.mv_rest_host.empty())
         if ((s = upload(A.mv_rest, A.mv_rest_host, st))) return s;
-    const size_t xbytes = std::max((size_t)(N * M) * sizeof(double), (size_t)(A.tw_on ? 4 * M * A.tw_S : 0) * sizeof(float));
+    const size_t xbytes = std::max((size_t)(L * M) * sizeof(double), (size_t)(A.tw_on ? 4 * M * A.tw_S : 0) * sizeof(float));
     if (A.mv_xT.n < xbytes)
         if ((s = dev_alloc(A.mv_xT, xbytes, st))) return s;
     CUDA_TRY(cudaStreamSynchronize(st));
@@ -1490,7 +1524,7 @@ static GradedArgs make_gargs(tdbem_asm *A) {
     const tdbem_mesh &m = *A->mesh;
     GradedArgs a{};
     a.g = make_geo(A);
-    a.N = (int)A->tg->N;
+    a.N = A->g_ncol;  // block columns (trial functions)
     a.tie = 1e-12 * A->tg->T;
     a.pair = (const double2 *)A->gpair.p;
     a.vmin = (const double *)A->gvmin.p;
@@ -1541,7 +1575,7 @@ static GradedArgs make_gargs(tdbem_asm *A) {
 // Window lengths per column and the batches of trial columns whose FP64
 // windows fit the staging budget; (re)allocates the staging buffers.
 static tdbem_status plan_graded_batches(tdbem_asm &A, double smax, cudaStream_t st) {
-    const int64_t N = A.tg->N, M = A.mesh->M, NB = A.mesh->NB;
+    const int64_t N = A.g_ncol, M = A.mesh->M, NB = A.mesh->NB;  // N: block columns
     A.g_kw.assign(N, 1);
     for (int64_t i = 0; i < N; ++i) A.g_kw[i] = graded_kw(A, i, smax);
     size_t fr = 0, tot = 0;
@@ -1600,10 +1634,11 @@ static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
     // ---- psi tables: FP32 set (24-point Gauss-Legendre x 4 per piece), FP64 sets (x 8), DCT
     const int nj32 = A->g_njob32, nj64 = A->g_nset64;
     launch_psi_samples_var(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p, (const int *)A->g_tib.p,
-                           (const double *)A->g_tr0.p, (const double *)A->g_tdr.p, nj32, (const double *)A->gl_x.p,
+                           (const int *)A->g_tm2.p, (const int *)A->g_tm1.p, (const double *)A->g_tr0.p, (const double *)A->g_tdr.p, nj32, (const double *)A->gl_x.p,
                            (const double *)A->gl_w.p, 24, 4, (double *)A->g_samples.p, st);
     launch_psi_samples_var(A->tg->kind, (const double *)A->tgrid.p, (int)A->tg->N, (const int *)A->g_tkb.p + nj32,
-                           (const int *)A->g_tib.p + nj32, (const double *)A->g_tr0.p + nj32,
+                           (const int *)A->g_tib.p + nj32, (const int *)A->g_tm2.p + nj32,
+                           (const int *)A->g_tm1.p + nj32, (const double *)A->g_tr0.p + nj32,
                            (const double *)A->g_tdr.p + nj32, nj64, (const double *)A->gl_x.p,
                            (const double *)A->gl_w.p, 24, 8, (double *)A->g_samples.p + (size_t)nj32 * NCHEB * 2, st);
     launch_psi_dct((const double *)A->g_samples.p, nj32 + nj64, (double *)A->g_coef.p, st);
@@ -1753,6 +1788,7 @@ tdbem_status tdbem_assemble_all(tdbem_asm *A, void *stream) {
 
 tdbem_status tdbem_assemble_block(tdbem_asm *A, int32_t k, int32_t i, void *stream) {
     if (!A) return fail(TDBEM_E_INVALID_ARG, "NULL assembler");
+    if (A->tg->p > 0) return fail(TDBEM_E_UNSUPPORTED, "one block on its own takes p = 0");
     const int64_t N = A->tg->N;
     if (k < 0 || k >= N || i < 0 || i >= N) return fail(TDBEM_E_INVALID_ARG, "block index out of range");
     if (i > k + 1) return fail(TDBEM_E_INVALID_ARG, "block above the first superdiagonal is zero (i > k + 1)");
@@ -1835,7 +1871,7 @@ static int mv_launches(const tdbem_asm *A) { return A->tw_on ? 3 : 2; }
 // the no-allocation entry point (xbytes usable bytes).
 static cudaError_t mv_launch(const tdbem_asm *A, const double *x, void *scratch, size_t xbytes, double *y, int nsm,
                              int variant, cudaStream_t st) {
-    const int64_t N = A->tg->N, M = A->mesh->M;
+    const int64_t N = time_rows(A), M = A->mesh->M;
     if (A->tw_on && (size_t)(4 * M * A->tw_S) * sizeof(float) <= xbytes) {
         // variants: 3 Toeplitz shapes (outputs per lane) x 2 CSR shapes
         cudaError_t e = launch_hessenberg_rest((const MvBlock *)A->mv_rest.p, (int)A->mv_rest_host.size(), x, y, M,
@@ -1862,7 +1898,7 @@ static cudaError_t mv_launch(const tdbem_asm *A, const double *x, void *scratch,
 static tdbem_status tune_matvec(const tdbem_asm *A, const double *x, double *y, int nsm, cudaStream_t st) {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
-    const int64_t N = A->tg->N, M = A->mesh->M;
+    const int64_t N = time_rows(A), M = A->mesh->M;
     const std::vector<int64_t> key = {dev, M, N, (int64_t)A->blocks.size(), A->fp64 ? 1 : 0, A->stats.nnz};
     {
         std::lock_guard<std::mutex> lock(g_mv_mu);
@@ -1901,7 +1937,7 @@ static tdbem_status tune_matvec(const tdbem_asm *A, const double *x, double *y, 
 tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
     if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
-    const int64_t N = A->tg->N, M = A->mesh->M;
+    const int64_t N = time_rows(A), M = A->mesh->M;
     const char *xb = (const char *)x, *yb = (const char *)y;
     const size_t bytes = (size_t)(N * M) * sizeof(double);
     if (xb < yb + bytes && yb < xb + bytes) return fail(TDBEM_E_INVALID_ARG, "x and y overlap");
@@ -1919,7 +1955,7 @@ tdbem_status tdbem_hessenberg_apply(const tdbem_asm *A, const double *x, double 
 
 tdbem_status tdbem_hessenberg_apply_noalloc(const tdbem_asm *A, const double *x, double *y, void *stream) {
     if (!A || !x || !y) return fail(TDBEM_E_INVALID_ARG, "NULL argument");
-    const int64_t N = A->tg->N, M = A->mesh->M;
+    const int64_t N = time_rows(A), M = A->mesh->M;
     if (N * M > MV_STATIC_MAX)
         return fail(TDBEM_E_INVALID_ARG, "N*M = " + std::to_string(N * M) + " exceeds the fixed scratch of " +
                                              std::to_string(MV_STATIC_MAX) + " doubles");
@@ -2002,7 +2038,7 @@ tdbem_status tdbem_rhs_assemble(const tdbem_asm *A, int32_t kind, const double *
     }
     const tdbem_asm *Ac = A;
     Geo g = make_geo(const_cast<tdbem_asm *>(Ac));
-    launch_rhs(A->tg->kind, g, (const double *)A->tgrid.p, (int)A->tg->N, A->tg->c, (const double *)A->rule_w64.p,
+    launch_rhs(A->tg->kind, g, (const double *)A->tgrid.p, (int)A->tg->N, A->tg->p + 1, A->tg->c, (const double *)A->rule_w64.p,
                (const double *)A->rule_l64.p, (const double *)A->gl_x.p, (const double *)A->gl_w.p, 24, 4, kind, prm,
                g_dev, (cudaStream_t)stream);
     CUDA_TRY(cudaGetLastError());
@@ -2018,7 +2054,7 @@ tdbem_status tdbem_solve_gmres(const tdbem_asm *A, const double *g, double *x, i
     if (!A->assembled) return fail(TDBEM_E_NOT_ASSEMBLED, "call tdbem_assemble_all first");
     if (restart < 1 || restart > GM_MAXV - 2) return fail(TDBEM_E_INVALID_ARG, "restart must be in 1..62");
     if (!(tol > 0.0) || max_iter < 1) return fail(TDBEM_E_INVALID_ARG, "need tol > 0 and max_iter >= 1");
-    const int64_t n = A->tg->N * A->mesh->M;
+    const int64_t n = time_rows(A) * A->mesh->M;
     const char *gb = (const char *)g, *xb = (const char *)x;
     if (gb < xb + n * 8 && xb < gb + n * 8) return fail(TDBEM_E_INVALID_ARG, "g and x overlap");
     cudaStream_t st = (cudaStream_t)stream;
@@ -2164,7 +2200,7 @@ tdbem_status tdbem_solve_dgmres(const tdbem_asm *A, const double *g, double *x, 
     if (l < 0) return fail(TDBEM_E_INVALID_ARG, "l must be >= 0");
     if (r < 0 || r > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "r must be in 0..62");
     if (!(tol > 0.0) || max_iter < 1) return fail(TDBEM_E_INVALID_ARG, "need tol > 0 and max_iter >= 1");
-    const int64_t n = A->tg->N * A->mesh->M;
+    const int64_t n = time_rows(A) * A->mesh->M;
     const char *gb = (const char *)g, *xb = (const char *)x;
     if (gb < xb + n * 8 && xb < gb + n * 8) return fail(TDBEM_E_INVALID_ARG, "g and x overlap");
     cudaStream_t st = (cudaStream_t)stream;
@@ -2395,6 +2431,7 @@ static tdbem_status krylov_setup(const tdbem_asm *A, int32_t restart, double tol
     if (levels > 0 && !inner) return fail(TDBEM_E_INVALID_ARG, "inner_iters is NULL");
     for (int l = 0; l < levels; ++l)
         if (inner[l] < 1 || inner[l] > KR_MAXM) return fail(TDBEM_E_INVALID_ARG, "inner iterations must be in 1..62");
+    if (A->tg->p > 0) return fail(TDBEM_E_UNSUPPORTED, "the block-Hessenberg preconditioner takes p = 0");
     const int64_t N = A->tg->N, M = A->mesh->M;
     const size_t bytes = (size_t)(N * M) * sizeof(double);
     const char *xb = (const char *)x, *yb = (const char *)y;

@@ -15,7 +15,7 @@ __device__ static double right_end(const double *t, int N, int i) { return i == 
 // psi_{k,i}(r) and psi~_{k,i}(r) of Eq. psis: integrate over the overlap of
 // the test support and the shifted trial support, split at the interior
 // breakpoints t_k and t_i + r, composite Gauss-Legendre on each piece.
-__device__ static void psi_direct(int bkind, const double *t, int N, int kb, int ib, double r,
+__device__ static void psi_direct(int bkind, const double *t, int N, int kb, int m2, int ib, int m1, double r,
                                   const double *gx, const double *gw, int gn, int gsub,
                                   double &psi, double &psit) {
     psi = 0.0; psit = 0.0;
@@ -38,8 +38,8 @@ __device__ static void psi_direct(int bkind, const double *t, int N, int kb, int
             for (int g = 0; g < gn; ++g) {
                 const double tt = a0 + w * gx[g];
                 double bk[3], bi[3];
-                basis(bkind, t, N, kb, tt, bk);
-                basis(bkind, t, N, ib, tt - r, bi);
+                basis_m(bkind, t, N, kb, m2, tt, bk);
+                basis_m(bkind, t, N, ib, m1, tt - r, bi);
                 s0 += w * gw[g] * bi[2] * bk[1];
                 s1 += w * gw[g] * bi[0] * bk[1];
             }
@@ -51,10 +51,12 @@ __device__ static void psi_direct(int bkind, const double *t, int N, int kb, int
 
 // One thread per (sub-panel, Chebyshev node). Sub-panel p covers
 // r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]); with pdr given, its
-// width is pdr[p] instead (uneven panels of a graded grid).
+// width is pdr[p] instead (uneven panels of a graded grid); with pm2, pm1
+// given, the block's test and trial temporal orders (else 0).
 __global__ void psi_samples_kernel(int bkind, const double *t, int N, const int *pkb, const int *pib,
-                                   const double *pr0, double dr, const double *pdr, int total, const double *gx,
-                                   const double *gw, int gn, int gsub, double *samples) {
+                                   const int *pm2, const int *pm1, const double *pr0, double dr, const double *pdr,
+                                   int total, const double *gx, const double *gw, int gn, int gsub,
+                                   double *samples) {
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= total * NCHEB) return;
     const int p = id / NCHEB, m = id % NCHEB;
@@ -62,7 +64,7 @@ __global__ void psi_samples_kernel(int bkind, const double *t, int N, const int 
     const double w = pdr ? pdr[p] : dr;
     const double r = pr0[p] + 0.5 * w * (xm + 1.0);
     double a, b;
-    psi_direct(bkind, t, N, pkb[p], pib[p], r, gx, gw, gn, gsub, a, b);
+    psi_direct(bkind, t, N, pkb[p], pm2 ? pm2[p] : 0, pib[p], pm1 ? pm1[p] : 0, r, gx, gw, gn, gsub, a, b);
     samples[2 * id + 0] = a;
     samples[2 * id + 1] = b;
 }
@@ -90,18 +92,20 @@ void launch_psi_samples(int bkind, const double *t, int N, const int *panel_clas
                         double *samples, cudaStream_t st) {
     (void)panel_class; (void)S;
     const int n = total_sub * NCHEB;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_r0,
-                                                       panel_dr, nullptr, total_sub, gl_x, gl_w, gl_n,
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, nullptr, nullptr,
+                                                       panel_r0, panel_dr, nullptr, total_sub, gl_x, gl_w, gl_n,
                                                        gl_sub, samples);
 }
 
 void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_kb, const int *panel_ib,
-                            const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
-                            const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st) {
+                            const int *panel_m2, const int *panel_m1, const double *panel_r0, const double *panel_dr,
+                            int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
+                            double *samples, cudaStream_t st) {
     const int n = total_sub * NCHEB;
     if (n <= 0) return;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_r0, 0.0, panel_dr,
-                                                       total_sub, gl_x, gl_w, gl_n, gl_sub, samples);
+    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_m2, panel_m1,
+                                                       panel_r0, 0.0, panel_dr, total_sub, gl_x, gl_w, gl_n, gl_sub,
+                                                       samples);
 }
 
 // Evaluation of one block's table at distances r (thread per r): the block
@@ -179,12 +183,12 @@ __device__ static double rhs_data(int kind, const double *prm, const double *x, 
 // One thread per (time index k, vertex l): the triangles around l, 7 points
 // each, and the support of bdot_k split at every grid point into `sub`
 // panels of gn Gauss-Legendre points (FP64).
-__global__ void rhs_kernel(int bkind, Geo g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
-                           const double *gx, const double *gw, int gn, int sub, int kind, RhsParams prm,
-                           double *out) {
+__global__ void rhs_kernel(int bkind, Geo g, const double *t, int N, int P1, double c, const double *rule_w,
+                           const double *rule_l, const double *gx, const double *gw, int gn, int sub, int kind,
+                           RhsParams prm, double *out) {
     const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= (int64_t)N * g.M) return;
-    const int k = (int)(id / g.M);
+    if (id >= (int64_t)N * P1 * g.M) return;
+    const int row = (int)(id / g.M), k = row / P1, mo = row % P1;  // time function b_{k,mo}: row k (p + 1) + mo
     const int64_t l = id % g.M;
     const int j0 = k == 0 ? 0 : k - 1, j1 = k == N - 1 ? N - 1 : k + 1;  // support [t_j0, t_j1]
     double acc = 0.0;
@@ -202,7 +206,7 @@ __global__ void rhs_kernel(int bkind, Geo g, const double *t, int N, double c, c
                     for (int m = 0; m < gn; ++m) {
                         const double s = t[j] + (sb + gx[m]) * h;
                         double b[3];
-                        basis(bkind, t, N, k, s, b);
+                        basis_m(bkind, t, N, k, mo, s, b);
                         it += gw[m] * h * b[1] * rhs_data(kind, prm.p, x, geo, s / c);
                     }
             }
@@ -212,12 +216,12 @@ __global__ void rhs_kernel(int bkind, Geo g, const double *t, int N, double c, c
     out[id] = acc;
 }
 
-void launch_rhs(int bkind, const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
-                const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
-                cudaStream_t st) {
-    const int64_t n = (int64_t)N * g.M;
-    rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bkind, g, t, N, c, rule_w, rule_l, gx, gw, gn, sub, kind, prm,
-                                                          out);
+void launch_rhs(int bkind, const Geo &g, const double *t, int N, int P1, double c, const double *rule_w,
+                const double *rule_l, const double *gx, const double *gw, int gn, int sub, int kind,
+                const RhsParams &prm, double *out, cudaStream_t st) {
+    const int64_t n = (int64_t)N * P1 * g.M;
+    rhs_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bkind, g, t, N, P1, c, rule_w, rule_l, gx, gw, gn, sub, kind,
+                                                          prm, out);
 }
 
 }  // namespace tdbem

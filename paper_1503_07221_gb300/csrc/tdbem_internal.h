@@ -124,9 +124,11 @@ void launch_psi_dct(const double *samples, int total_sub, double *coef, cudaStre
 void launch_psi_table(const double *r, int64_t n, double inv_dt, int lag, int rho, int P, int panel0, int S,
                       const double *c64, const ChebF32 &c32, int use32, double *out, cudaStream_t st);
 // sub-panel p covers [r0[p], r0[p] + dr[p]] (uneven panels)
+// (panel_m2, panel_m1: temporal orders of each panel's block, or null for 0)
 void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_kb, const int *panel_ib,
-                            const double *panel_r0, const double *panel_dr, int total_sub, const double *gl_x,
-                            const double *gl_w, int gl_n, int gl_sub, double *samples, cudaStream_t st);
+                            const int *panel_m2, const int *panel_m1, const double *panel_r0, const double *panel_dr,
+                            int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
+                            double *samples, cudaStream_t st);
 
 // pattern.cu
 void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st);
@@ -283,9 +285,9 @@ enum { RHS_PLANE_WAVE = 0, RHS_SPHERE_N0 = 1, RHS_SPHERE_N1 = 2 };
 struct RhsParams {
     double p[5];
 };
-void launch_rhs(int bkind, const Geo &g, const double *t, int N, double c, const double *rule_w, const double *rule_l,
-                const double *gx, const double *gw, int gn, int sub, int kind, const RhsParams &prm, double *out,
-                cudaStream_t st);
+void launch_rhs(int bkind, const Geo &g, const double *t, int N, int P1, double c, const double *rule_w,
+                const double *rule_l, const double *gx, const double *gw, int gn, int sub, int kind,
+                const RhsParams &prm, double *out, cudaStream_t st);
 // solve.cu: vector kernels of the GMRES solver
 void launch_multi_dot(const double *V, int64_t ld, int nv, const double *w, int64_t n, double *partial, double *h,
                       cudaStream_t st, const int *active = nullptr);

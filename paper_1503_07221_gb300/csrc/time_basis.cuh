@@ -1,5 +1,6 @@
-// Device time basis of Sec. 3 (Eq. BasisFunctions, p = 0) shared by the
-// psi-table build (table.cu) and the potential evaluation (potential.cu).
+// Device time basis of Sec. 3 (Eq. BasisFunctions) shared by the psi-table
+// build (table.cu) and the potential evaluation (potential.cu): the p = 0
+// functions (basis) and those of order m (basis_m).
 #pragma once
 #include <math.h>
 
@@ -88,4 +89,41 @@ __device__ static inline void basis(int kind, const double *t, int N, int i, dou
     else falling(kind, s, t[i], t[i + 1] - t[i], out);
 }
 
+// Legendre polynomial P_m and its first two derivatives at x, from the
+// three-term recurrence (n + 1) P_{n+1} = (2n + 1) x P_n - n P_{n-1} and
+// P'_{n+1} = P'_{n-1} + (2n + 1) P_n, P''_{n+1} = P''_{n-1} + (2n + 1) P'_n.
+__device__ static inline void legendre3(int m, double x, double out[3]) {
+    double p0 = 1.0, d0 = 0.0, e0 = 0.0;  // P_n, P'_n, P''_n at n = 0
+    double pm = 0.0, dm = 0.0, em = 0.0;  // n - 1
+    for (int n = 0; n < m; ++n) {
+        const double p1 = ((2 * n + 1) * x * p0 - n * pm) / (n + 1);
+        const double d1 = dm + (2 * n + 1) * p0, e1 = em + (2 * n + 1) * d0;
+        pm = p0; dm = d0; em = e0;
+        p0 = p1; d0 = d1; e0 = e1;
+    }
+    out[0] = p0; out[1] = d0; out[2] = e0;
+}
+
+// Time basis function b_{i,m} of order m (Eq. BasisFunctions): the p = 0
+// function of basis() times the Legendre polynomial P_m of the coordinate
+// that maps its support onto [-1, 1]:
+//   i = 0:     P_m(2 s / h - 1),            h = t_1 - t_0
+//   inner i:   P_m(2 (s - t_{i-1}) / (t_{i+1} - t_{i-1}) - 1)  (= (s - t_{i-1})/dt - 1 when equidistant)
+//   i = N-1:   P_m(2 (s - t_{N-2}) / h - 1), h = t_{N-1} - t_{N-2};
+// with the first two derivatives by the product rule.
+__device__ static inline void basis_m(int kind, const double *t, int N, int i, int m, double s, double out[3]) {
+    basis(kind, t, N, i, s, out);
+    if (m == 0 || (out[0] == 0.0 && out[1] == 0.0 && out[2] == 0.0)) return;
+    double a, c;
+    if (i == 0) { a = 2.0 / (t[1] - t[0]); c = -1.0 - a * t[0]; }
+    else if (i == N - 1) { a = 2.0 / (t[N - 1] - t[N - 2]); c = -1.0 - a * t[N - 2]; }
+    else { a = 2.0 / (t[i + 1] - t[i - 1]); c = -1.0 - a * t[i - 1]; }
+    double L[3];
+    legendre3(m, a * s + c, L);
+    const double l0 = L[0], l1 = a * L[1], l2 = a * a * L[2];
+    const double b0 = out[0], b1 = out[1], b2 = out[2];
+    out[0] = b0 * l0;
+    out[1] = b1 * l0 + b0 * l1;
+    out[2] = b2 * l0 + 2.0 * b1 * l1 + b0 * l2;
+}
 }  // namespace tdbem

@@ -183,6 +183,8 @@ class TimeGrid:
         _check(lib().tdbem_timegrid_create(t.ctypes.data, t.size, p, basis_kind, c, C.byref(h)))
         self.h = h
         self.N = t.size
+        self.p = int(p)
+        self.L = self.N * (self.p + 1)  # time functions: rows of x and y
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -270,7 +272,7 @@ class Assembler:
         noalloc=True calls tdbem_hessenberg_apply_noalloc (fixed scratch,
         N*M <= 2^21); y must then be given."""
         import torch
-        shape = (self.grid.N, self.mesh.M)
+        shape = (self.grid.L, self.mesh.M)
         for name, v in (("x", x), ("y", y)):
             if v is not None and (tuple(v.shape) != shape or v.dtype != torch.float64 or not v.is_cuda
                                   or not v.is_contiguous()):
@@ -284,9 +286,10 @@ class Assembler:
         return y
 
     def rhs(self, kind, params=(), out=None, stream=None):
-        """Right-hand side g_k(l) as a float64 CUDA tensor of shape (N, M)."""
+        """Right-hand side g_{k,m}(l) as a float64 CUDA tensor of shape (N (p + 1), M),
+        row k (p + 1) + m."""
         import torch
-        shape = (self.grid.N, self.mesh.M)
+        shape = (self.grid.L, self.mesh.M)
         if out is None:
             out = torch.empty(shape, dtype=torch.float64, device="cuda")
         p = np.ascontiguousarray(params, dtype=np.float64)

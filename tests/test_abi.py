@@ -60,8 +60,11 @@ def test_timegrid_validation(L):
         with pytest.raises(tdbem.TdbemError) as e:
             tdbem.TimeGrid(np.array(bad))
         assert e.value.code == 3
+    # temporal degree p = 0, 1, 2 (Eq. BasisFunctions); 3 is not built
+    for p in (0, 1, 2):
+        tdbem.TimeGrid(np.linspace(0, 1, 5), p=p)
     with pytest.raises(tdbem.TdbemError) as e:
-        tdbem.TimeGrid(np.linspace(0, 1, 5), p=1)
+        tdbem.TimeGrid(np.linspace(0, 1, 5), p=3)
     assert e.value.code == 8
     with pytest.raises(tdbem.TdbemError) as e:
         tdbem.TimeGrid(np.linspace(0, 1, 5), c=-1.0)
