@@ -1732,7 +1732,9 @@ static tdbem_status assemble_graded(tdbem_asm *A, cudaStream_t st) {
             ga.color_tris = (const int32_t *)A->colors.p + A->color_off[c];
             ga.ncolor = A->color_off[c + 1] - A->color_off[c];
             if (ga.ncolor <= 0) continue;
-            launch_gnear(ga, (int)std::min<int64_t>(ga.ncolor, 4 * (int64_t)nsm), st);
+            // mixed, p = 0: psi in FP32; p >= 1 keeps FP64 (the Legendre factors
+            // left 1.2e-6 per block with FP32 on the 80-triangle sphere)
+            launch_gnear(ga, !A->fp64 && A->tg->p == 0, (int)std::min<int64_t>(ga.ncolor, 4 * (int64_t)nsm), st);
             ++launches;
         }
         CUDA_TRY(cudaGetLastError());

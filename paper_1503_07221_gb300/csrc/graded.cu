@@ -622,7 +622,13 @@ void launch_gfar(const GradedArgs &a, bool fp64, int grid, size_t smem, cudaStre
 // another (they share vertices among themselves). Point pairs of the
 // Sauter-Schwab rule are staged GN_TILE at a time (FP64 r, weight / r and the
 // barycentrics); the kept blocks of every batch column are the items, one
-// warp per item, lanes over the staged point pairs, FP64 tables throughout.
+// warp per item, lanes over the staged point pairs. FP64 path: FP64 tables
+// throughout. F32 (mixed path): per point pair r as an FP32 pair and the
+// weight w / r as an FP32 pair; per (point pair, block) the panel found in
+// FP32, its argument from the FP32-pair distance against the panel's midpoint
+// pair, psi and psi~ from the panel's FP32 expansion with the residuals of
+// its leading coefficients (g_cheb32), and the nine sums S_ab and S~ as FP32
+// pairs (two-sum), added across the warp in FP64.
 __device__ static inline double g_dsum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -631,8 +637,17 @@ __device__ static inline double g_dsum(double v) {
 
 constexpr int GN_ITEMS = 256;
 
+__device__ __forceinline__ void gn_two_sum_add(float &h, float &l, float v) {
+    const float s = h + v;
+    const float bb = s - h;
+    l += (h - (s - bb)) + (v - bb);
+    h = s;
+}
+
+template <bool F32>
 __global__ void __launch_bounds__(GN_WARPS * 32) gnear_kernel(const GradedArgs A) {
     __shared__ double q[GN_TILE * 6];
+    __shared__ float qf[F32 ? GN_TILE * 8 : 1];  // rh, rl, wh, wl, lx0, lx1, ly0, ly1
     __shared__ double acc[GN_ITEMS * 10];
     __shared__ int items[GN_ITEMS];  // (batch column << 16) | (k - k0 of that column)
     __shared__ int nitems, ntotal;
@@ -711,11 +726,20 @@ __global__ void __launch_bounds__(GN_WARPS * 32) gnear_kernel(const GradedArgs A
                             r2 += (xd - yd) * (xd - yd);
                         }
                         const double r = sqrt(r2);
-                        double *qq = q + 6 * p;
-                        qq[0] = r;
-                        qq[1] = rr[4] * scale / r;
-                        qq[2] = 1.0 - xh0; qq[3] = xh0 - xh1;
-                        qq[4] = 1.0 - yh0; qq[5] = yh0 - yh1;
+                        if constexpr (F32) {
+                            float *qq = qf + 8 * p;
+                            const double wr = rr[4] * scale / r;
+                            qq[0] = (float)r; qq[1] = (float)(r - (double)qq[0]);
+                            qq[2] = (float)wr; qq[3] = (float)(wr - (double)qq[2]);
+                            qq[4] = (float)(1.0 - xh0); qq[5] = (float)(xh0 - xh1);
+                            qq[6] = (float)(1.0 - yh0); qq[7] = (float)(yh0 - yh1);
+                        } else {
+                            double *qq = q + 6 * p;
+                            qq[0] = r;
+                            qq[1] = rr[4] * scale / r;
+                            qq[2] = 1.0 - xh0; qq[3] = xh0 - xh1;
+                            qq[4] = 1.0 - yh0; qq[5] = yh0 - yh1;
+                        }
                     }
                     __syncthreads();
                     for (int it = w; it < ni; it += GN_WARPS) {
@@ -724,7 +748,38 @@ __global__ void __launch_bounds__(GN_WARPS * 32) gnear_kernel(const GradedArgs A
                         const double ba = A.ga[cb], bb = A.gb[cb];
                         const int pg = A.pan0[cb], npn = A.pan0[cb + 1] - pg;
                         double Sab[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, St = 0.0;
-                        for (int p = lane; p < np; p += 32) {
+                        if constexpr (F32) {
+                            const float ba32 = (float)ba, bb32 = (float)bb;
+                            float Sh[9], Sl[9], Th = 0.f, Tl = 0.f;
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) Sh[e] = Sl[e] = 0.f;
+                            for (int p = lane; p < np; p += 32) {
+                                const float *qq = qf + 8 * p;
+                                const float rh = qq[0], rl = qq[1];
+                                if (!(rh > ba32 && rh < bb32)) continue;
+                                int pp = 0;
+                                while (pp + 1 < npn && rh >= A.pan32[pg + pp + 1].x) ++pp;
+                                const float4 mt = A.pan32[pg + pp];  // (start_h, mid_h, mid_l, 2 / width)
+                                const float x = ((rh - mt.y) + (rl - mt.z)) * mt.w;
+                                float ps, pt;
+                                g_cheb32(reinterpret_cast<const float4 *>(A.coef32) + (size_t)(pg + pp) * GC32, x, ps,
+                                         pt);
+                                const float wp = fmaf(qq[3], ps, qq[2] * ps), wt = fmaf(qq[3], pt, qq[2] * pt);
+                                const float lx[3] = {qq[4], qq[5], 1.f - qq[4] - qq[5]};
+                                const float ly[3] = {qq[6], qq[7], 1.f - qq[6] - qq[7]};
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) {
+                                    const float wa = wp * lx[a];
+#pragma unroll
+                                    for (int b = 0; b < 3; ++b) gn_two_sum_add(Sh[3 * a + b], Sl[3 * a + b], wa * ly[b]);
+                                }
+                                gn_two_sum_add(Th, Tl, wt);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 9; ++e) Sab[e] = (double)Sh[e] + (double)Sl[e];
+                            St = (double)Th + (double)Tl;
+                        }
+                        for (int p = lane; !F32 && p < np; p += 32) {
                             const double *qq = q + 6 * p;
                             const double r = qq[0];
                             if (!(r > ba && r < bb)) continue;
@@ -770,9 +825,10 @@ __global__ void __launch_bounds__(GN_WARPS * 32) gnear_kernel(const GradedArgs A
     }
 }
 
-void launch_gnear(const GradedArgs &a, int grid, cudaStream_t st) {
+void launch_gnear(const GradedArgs &a, bool f32, int grid, cudaStream_t st) {
     if (grid <= 0) return;
-    gnear_kernel<<<grid, GN_WARPS * 32, 0, st>>>(a);
+    if (f32) gnear_kernel<true><<<grid, GN_WARPS * 32, 0, st>>>(a);
+    else gnear_kernel<false><<<grid, GN_WARPS * 32, 0, st>>>(a);
 }
 
 // ----------------------------------------------------------- vertex bounds

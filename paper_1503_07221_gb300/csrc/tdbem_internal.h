@@ -424,7 +424,7 @@ struct GradedArgs {
     int *status;
 };
 void launch_gfar(const GradedArgs &a, bool fp64, int grid, size_t smem, cudaStream_t st);
-void launch_gnear(const GradedArgs &a, int grid, cudaStream_t st);
+void launch_gnear(const GradedArgs &a, bool f32, int grid, cudaStream_t st);
 // per (row, column): far and near row counts of every block of the column
 void launch_gcount(const GradedArgs &a, const int *cb2api, const int64_t *nbr_ptr, const int32_t *nbr,
                    int64_t *cnt_far, int64_t *cnt_near, cudaStream_t st);
