@@ -402,6 +402,8 @@ struct tdbem_asm {
     // mixed path on an equidistant grid: the Toeplitz class (inner blocks
     // (k, 1) and (1, 2)) as per-pair lag windows (toeplitz.cu), every other
     // block by the CSR kernel (mv_rest)
+    DevBuf pb_list, pb_cnt;
+    int64_t pb_cap = 0;
     bool tw_on = false;
     int tw_TL = 8, tw_S = 0, tw_PADL = 0;
     int64_t tw_nfar = 0, tw_nnear = 0;
@@ -1032,6 +1034,10 @@ tdbem_status tdbem_assembler_create(const tdbem_mesh *mesh, const tdbem_timegrid
     const size_t MM = (size_t)M * M;
     const size_t rs = A->fp64 ? 8 : 4;
     if ((s = dev_alloc(A->rec, (size_t)E * E * sizeof(PairRec), st))) return bail(s);
+    // pairs whose FP32 lag decision is not certain, decided by a dense FP64 pass
+    A->pb_cap = std::min<int64_t>(std::max<int64_t>(PB_LIST_MIN, E * E / 64), std::max<int64_t>(E * E, 1));
+    if ((s = dev_alloc(A->pb_list, (size_t)A->pb_cap * sizeof(int64_t), st))) return bail(s);
+    if ((s = dev_alloc(A->pb_cnt, 16, st))) return bail(s);
     if ((s = dev_alloc(A->wdlo, 3 * MM * sizeof(int16_t), st))) return bail(s);
     if ((s = dev_alloc(A->wdhi, 3 * MM * sizeof(int16_t), st))) return bail(s);
     if ((s = dev_alloc(A->wsmask, MM, st))) return bail(s);
@@ -1285,7 +1291,13 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     // ---- element-pair bounds, vertex-pair windows
     Geo g = make_geo(A);
     LagTables lt = make_lt(A);
-    launch_pair_bounds(g, lt, (PairRec *)A->rec.p, st);
+    {
+        int dev = 0, nsm0 = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev));
+        launch_pair_bounds(g, lt, (PairRec *)A->rec.p, (int64_t *)A->pb_list.p, A->pb_cap,
+                           (unsigned long long *)A->pb_cnt.p, (int *)A->status.p, nsm0, st);
+    }
     launch_vertex_windows(g, (const PairRec *)A->rec.p, (int16_t *)A->wdlo.p, (int16_t *)A->wdhi.p,
                           (uint8_t *)A->wsmask.p, A->KW, (int *)A->status.p, st);
     {
@@ -1464,11 +1476,11 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
     A->stats.ms_extract = ms[3];
     A->stats.ms_total = ms[0] + ms[1] + ms[2] + ms[3];
     {
-        // tables 4, bounds + windows + counter 3, row counts 1, scans 2, fills 2,
+        // tables 4, bounds (two passes) + windows + counter 4, row counts 1, scans 2, fills 2,
         // and per colour: far, near (+ far special blocks in the mixed path)
         int64_t ncol = 0;
         for (size_t c = 0; c + 1 < A->color_off.size(); ++c) ncol += A->color_off[c + 1] > A->color_off[c];
-        A->stats.kernel_launches = 12 + ncol * (A->fp64 ? 2 : 3) + (A->tw_on ? 3 : 0);
+        A->stats.kernel_launches = 13 + ncol * (A->fp64 ? 2 : 3) + (A->tw_on ? 3 : 0);
     }
     if (status) return fail(TDBEM_E_DEVICE, "kernel status word " + std::to_string(status));
     if ((s = plan_matvec(*A, st))) return s;

@@ -174,7 +174,9 @@ __device__ static void decide32(const float *thr, const int *off, const LagTable
 // between them and the exact FP64 distance decides the same; only where they
 // differ is the pair recomputed exactly in FP64 and decided in FP64. The
 // decisions are therefore those of the FP64 computation.
-__device__ static void pair_bounds_one(const Geo &g, const LagTables &lt, PairRec *rec, int64_t q, int64_t s,
+// FP32 pass for one pair: writes the record when the two ends agree and
+// returns false; returns true when the pair needs the FP64 decision.
+__device__ static bool pair_bounds_one(const Geo &g, const LagTables &lt, PairRec *rec, int64_t q, int64_t s,
                                        const float *pb_thr, const int *pb_off, float tmax) {
     const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
     int shared = 0;
@@ -198,21 +200,34 @@ __device__ static void pair_bounds_one(const Geo &g, const LagTables &lt, PairRe
     decide32(pb_thr, pb_off, lt, hn, hx + mg, r1);
     bool same = r0.smask == r1.smask;
     for (int c = 0; c < NLAG; ++c) same = same && r0.lo[c] == r1.lo[c] && r0.cnt[c] == r1.cnt[c];
+    if (!same) return true;
     PairRec r = r0;
-    if (!same) {
-        d3 ad[3], bd[3];
-        for (int i = 0; i < 3; ++i) { ad[i] = ld3(g.V + 3 * A[i]); bd[i] = ld3(g.V + 3 * B[i]); }
-        double dn2, dx2;
-        tri_bounds2<d3, double>(ad, bd, shared != 0, dn2, dx2);
-        decide(lt, sqrt(dn2), sqrt(dx2), r);
-    }
+    r.adj = (uint8_t)shared;
+    for (int k = 0; k < 5; ++k) r.pad[k] = 0;
+    rec[q * g.E + s] = r;
+    return false;
+}
+
+// FP64 decision of one pair (exact bounds, FP64 decide)
+__device__ static void pair_bounds_fp64(const Geo &g, const LagTables &lt, PairRec *rec, int64_t q, int64_t s) {
+    const int32_t *A = g.F + 3 * q, *B = g.F + 3 * s;
+    int shared = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) shared += (A[i] == B[j]);
+    d3 ad[3], bd[3];
+    for (int i = 0; i < 3; ++i) { ad[i] = ld3(g.V + 3 * A[i]); bd[i] = ld3(g.V + 3 * B[i]); }
+    double dn2, dx2;
+    tri_bounds2<d3, double>(ad, bd, shared != 0, dn2, dx2);
+    PairRec r;
+    decide(lt, shared ? 0.0 : sqrt(dn2), sqrt(dx2), r);
     r.adj = (uint8_t)shared;
     for (int k = 0; k < 5; ++k) r.pad[k] = 0;
     rec[q * g.E + s] = r;
 }
 
 // One CTA per test triangle q, its threads over the trial triangles.
-__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
+__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec, int64_t *list, int64_t cap,
+                                   unsigned long long *cnt, int *status) {
     extern __shared__ float pb_thr[];
     __shared__ int pb_off[NCLASS + 1];
     __shared__ float pb_tmax;
@@ -240,15 +255,44 @@ __global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec) {
     }
     __syncthreads();
     const int64_t q = blockIdx.x;  // test
-    for (int64_t s = threadIdx.x; s < g.E; s += blockDim.x)  // trial
-        pair_bounds_one(g, lt, rec, q, s, pb_thr, pb_off, pb_tmax);
+    const int lane = threadIdx.x & 31;
+    for (int64_t s0 = 0; s0 < g.E; s0 += blockDim.x) {  // trial
+        const int64_t s = s0 + threadIdx.x;
+        const bool need = s < g.E && pair_bounds_one(g, lt, rec, q, s, pb_thr, pb_off, pb_tmax);
+        // the pairs that need FP64 go to a list for a dense second pass (one
+        // atomic per warp; the FP64 code stays out of this kernel, which keeps
+        // its registers low); past the list's capacity the status flags it
+        const unsigned bal = __ballot_sync(0xffffffffu, need);
+        if (!bal) continue;
+        unsigned long long base = 0;
+        if (lane == __ffs(bal) - 1) base = atomicAdd(cnt, (unsigned long long)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, __ffs(bal) - 1);
+        if (need) {
+            const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
+            if (idx < (unsigned long long)cap) list[idx] = q * g.E + s;
+            else *status |= ST_PBLIST;
+        }
+    }
+}
+
+// the listed pairs, one thread each
+__global__ void pair_bounds_list_kernel(Geo g, LagTables lt, PairRec *rec, const int64_t *list, int64_t cap,
+                                        const unsigned long long *cnt) {
+    const int64_t n = min((int64_t)*cnt, cap);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t id = list[i];
+        pair_bounds_fp64(g, lt, rec, id / g.E, id % g.E);
+    }
 }
 
 
-void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st) {
+void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, int64_t *list, int64_t cap,
+                        unsigned long long *cnt, int *status, int nsm, cudaStream_t st) {
     int nthr = 0;
     for (int c = 0; c < NCLASS; ++c) nthr += 2 * std::max(lt.dhi[c] - lt.dlo[c] + 1, 0);
-    pair_bounds_kernel<<<(unsigned)g.E, 256, (size_t)nthr * sizeof(float), st>>>(g, lt, rec);
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st);
+    pair_bounds_kernel<<<(unsigned)g.E, 256, (size_t)nthr * sizeof(float), st>>>(g, lt, rec, list, cap, cnt, status);
+    pair_bounds_list_kernel<<<nsm * 8, 128, 0, st>>>(g, lt, rec, list, cap, cnt);
 }
 
 // Graded grids: exact FP64 bounds (dmin, dmax) of every element pair (dmin

@@ -70,6 +70,7 @@ enum {
     ST_NEAR_ORDER = 4,     // near rule too large for shared memory
     ST_NBR = 8,            // near neighbour lookup failed
     ST_WAIT = 16,          // a bounded wait inside a kernel gave up
+    ST_PBLIST = 32,        // the list of element pairs for the FP64 bound decisions overflowed
 };
 
 // Element-pair record of the bounds pass: kept lag range per lag class and a
@@ -131,7 +132,13 @@ void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_
                             double *samples, cudaStream_t st);
 
 // pattern.cu
-void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, cudaStream_t st);
+// FP32 pass over all element pairs, then a dense FP64 pass over the pairs
+// whose FP32 decision was not certain (list of capacity cap, count in cnt;
+// capacity max(2^24, E^2 / 64), several times the uncertain share seen; an
+// overflow sets ST_PBLIST in status)
+constexpr int64_t PB_LIST_MIN = (int64_t)1 << 24;
+void launch_pair_bounds(const Geo &g, const LagTables &lt, PairRec *rec, int64_t *list, int64_t cap,
+                        unsigned long long *cnt, int *status, int nsm, cudaStream_t st);
 // graded grids: exact (dmin, dmax) of every element pair, E x E
 void launch_gpair_bounds(const Geo &g, double2 *out, cudaStream_t st);
 void launch_vertex_windows(const Geo &g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
