@@ -226,7 +226,7 @@ __device__ static void pair_bounds_fp64(const Geo &g, const LagTables &lt, PairR
 }
 
 // One CTA per test triangle q, its threads over the trial triangles.
-__global__ void pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec, int64_t *list, int64_t cap,
+__global__ void __launch_bounds__(256, 4) pair_bounds_kernel(Geo g, LagTables lt, PairRec *rec, int64_t *list, int64_t cap,
                                    unsigned long long *cnt, int *status) {
     extern __shared__ float pb_thr[];
     __shared__ int pb_off[NCLASS + 1];
