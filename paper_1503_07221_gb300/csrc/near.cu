@@ -179,14 +179,17 @@ near_kernel(const NearArgs A) {
 // near r = 0 or near the corner lag) for element pairs WITHOUT a shared
 // vertex, in FP64 with the 7-point rule on both triangles; used by the mixed
 // path, whose FP32 kernel evaluates only the three lag classes. One CTA per
-// test triangle of the current colour scans its pair records in trial order
-// and processes the qualifying pairs one after another with one warp (lanes
-// over the 49 point pairs), adding into the far special-block windows.
+// test triangle of the current colour scans its pair records in trial order;
+// its four warps take the qualifying pairs four at a time (lanes over the 49
+// point pairs), and warp 0 adds their values into the far special-block
+// windows in list order.
 constexpr int FS_THREADS = 128;
+constexpr int FS_WARPS = FS_THREADS / 32;
 __global__ void __launch_bounds__(FS_THREADS)
 farspec_kernel(const NearArgs A) {
     __shared__ int list[FS_THREADS];
     __shared__ int nlist;
+    __shared__ double fs_val[FS_WARPS][NSPEC][9];  // one list entry per warp: its special-block values
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Geo &g = A.g;
     const int64_t M = g.M, E = g.E, MM = M * M;
@@ -216,8 +219,12 @@ farspec_kernel(const NearArgs A) {
                 nlist = t;
             }
             __syncthreads();
-            if (w == 0) {
-                for (int q = 0; q < nlist; ++q) {
+            // four list entries at a time, one per warp, into shared memory;
+            // then warp 0 adds them in list order (entries can share a vertex
+            // pair, so the adds stay in one fixed order)
+            for (int q0 = 0; q0 < nlist; q0 += FS_WARPS) {
+                const int q = q0 + w;
+                if (q < nlist) {
                     const int64_t s2 = list[q];
                     const PairRec r2 = A.rec[tau * E + s2];
                     double nn = 0.0;
@@ -269,12 +276,22 @@ farspec_kernel(const NearArgs A) {
                             const int a = lane / 3, b = lane % 3;
                             const double *ct = g.geo64 + 16 * tau + 4 + 3 * a, *cs = g.geo64 + 16 * s2 + 4 + 3 * b;
                             const double cc = ct[0] * cs[0] + ct[1] * cs[1] + ct[2] * cs[2];
-                            const int64_t l = g.F[3 * tau + a], j = g.F[3 * s2 + b];
-                            if ((A.smask[l * M + j] >> sb) & 1u)
-                                A.far_spec[sb * MM + l * M + j] += nn * Sab[a][b] + cc * St;
+                            fs_val[w][sb][lane] = nn * Sab[a][b] + cc * St;
                         }
                     }
                 }
+                __syncthreads();
+                if (w == 0 && lane < 9)
+                    for (int k = 0; k < FS_WARPS && q0 + k < nlist; ++k) {
+                        const int64_t s2 = list[q0 + k];
+                        const PairRec r2 = A.rec[tau * E + s2];
+                        const int a = lane / 3, b = lane % 3;
+                        const int64_t l = g.F[3 * tau + a], j = g.F[3 * s2 + b];
+                        for (int sb = 0; sb < NSPEC; ++sb)
+                            if (((r2.smask >> sb) & 1u) && ((A.smask[l * M + j] >> sb) & 1u))
+                                A.far_spec[sb * MM + l * M + j] += fs_val[k][sb][lane];
+                    }
+                __syncthreads();
             }
             __syncthreads();
         }
