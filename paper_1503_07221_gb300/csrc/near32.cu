@@ -29,6 +29,9 @@ namespace tdbem {
 constexpr int N32_WARPS = 8;
 constexpr int N32_THREADS = N32_WARPS * 32;
 constexpr int N32_CELLS = 16;  // lag cells floor(q) a near point pair can occupy
+// point chunks of N32_THREADS in the sort: 4096 point pairs, above the largest
+// rule (near_order <= 5: 6 x 5^4 = 3750 for identical triangles)
+constexpr int N32_MAXCHK = 16;
 
 // one point pair: Chebyshev argument, weight w / r as an FP32 pair, the two
 // free barycentrics of each side, and the cell floor(q)
@@ -50,7 +53,7 @@ __device__ static inline double n32_dsum_warp(double v) {
     return v;
 }
 
-__global__ void __launch_bounds__(N32_THREADS) near32_kernel(const NearArgs A, const ChebF32 C, int npp_max) {
+__global__ void __launch_bounds__(N32_THREADS, 3) near32_kernel(const NearArgs A, const ChebF32 C, int npp_max) {
     extern __shared__ __align__(16) unsigned char n32_raw[];
     NearPt32 *pts = reinterpret_cast<NearPt32 *>(n32_raw);
     int16_t *order = reinterpret_cast<int16_t *>(pts + npp_max);
@@ -59,7 +62,8 @@ __global__ void __launch_bounds__(N32_THREADS) near32_kernel(const NearArgs A, c
     __shared__ int items[64];
     __shared__ int nitems;
     __shared__ int bstart[N32_CELLS + 1];
-    __shared__ int wcnt[N32_WARPS];
+    __shared__ int scnt[N32_CELLS * N32_MAXCHK * N32_WARPS];  // per (cell, chunk, warp): count, then offset
+    __shared__ int ctot[N32_CELLS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const Geo &g = A.g;
     const int64_t M = g.M, E = g.E, MM = M * M;
@@ -118,29 +122,49 @@ __global__ void __launch_bounds__(N32_THREADS) near32_kernel(const NearArgs A, c
             }
             __syncthreads();
             // stable counting sort of the point pairs by lag cell: a block's
-            // support is then one contiguous run of the order (no idle lanes)
+            // support is then one contiguous run of the order (no idle lanes).
+            // Counts per (point chunk k, warp, cell) by ballots, offsets in
+            // the order (cell, k, warp, lane) = (cell, point index), scatter.
             {
-                int base = 0;
-                for (int cb = 0; cb < N32_CELLS; ++cb) {
-                    if (threadIdx.x == 0) bstart[cb] = base;
-                    for (int p0 = 0; p0 < npp; p0 += N32_THREADS) {
-                        const int p = p0 + threadIdx.x;
-                        int cl = N32_CELLS;
-                        if (p < npp) cl = min(pts[p].cell, N32_CELLS - 1);
-                        const bool in = cl == cb;
-                        const unsigned bal = __ballot_sync(0xffffffffu, in);
-                        if (lane == 0) wcnt[w] = __popc(bal);
-                        __syncthreads();
-                        int off = base;
-                        for (int k = 0; k < w; ++k) off += wcnt[k];
-                        if (in) order[off + __popc(bal & ((1u << lane) - 1u))] = (int16_t)p;
-                        int tot = 0;
-                        for (int k = 0; k < N32_WARPS; ++k) tot += wcnt[k];
-                        __syncthreads();
-                        base += tot;
+                const int nchk = (npp + N32_THREADS - 1) / N32_THREADS;
+                for (int k = 0; k < nchk; ++k) {
+                    const int p = k * N32_THREADS + threadIdx.x;
+                    const int cl = p < npp ? min(pts[p].cell, N32_CELLS - 1) : N32_CELLS;
+                    for (int cb = 0; cb < N32_CELLS; ++cb) {
+                        const unsigned bal = __ballot_sync(0xffffffffu, cl == cb);
+                        if (lane == 0) scnt[(cb * N32_MAXCHK + k) * N32_WARPS + w] = __popc(bal);
                     }
                 }
-                if (threadIdx.x == 0) bstart[N32_CELLS] = base;
+                __syncthreads();
+                if (threadIdx.x < N32_CELLS) {
+                    int tot = 0;
+                    for (int i = 0; i < nchk * N32_WARPS; ++i) tot += scnt[threadIdx.x * N32_MAXCHK * N32_WARPS + i];
+                    ctot[threadIdx.x] = tot;
+                }
+                __syncthreads();
+                if (threadIdx.x < N32_CELLS) {
+                    int base = 0;
+                    for (int cb = 0; cb < (int)threadIdx.x; ++cb) base += ctot[cb];
+                    bstart[threadIdx.x] = base;
+                    if (threadIdx.x == N32_CELLS - 1) bstart[N32_CELLS] = base + ctot[threadIdx.x];
+                    int *c = scnt + threadIdx.x * N32_MAXCHK * N32_WARPS;
+                    for (int i = 0; i < nchk * N32_WARPS; ++i) {  // counts -> offsets in place
+                        const int v = c[i];
+                        c[i] = base;
+                        base += v;
+                    }
+                }
+                __syncthreads();
+                for (int k = 0; k < nchk; ++k) {
+                    const int p = k * N32_THREADS + threadIdx.x;
+                    const int cl = p < npp ? min(pts[p].cell, N32_CELLS - 1) : N32_CELLS;
+                    for (int cb = 0; cb < N32_CELLS; ++cb) {
+                        const unsigned bal = __ballot_sync(0xffffffffu, cl == cb);
+                        if (cl == cb)
+                            order[scnt[(cb * N32_MAXCHK + k) * N32_WARPS + w] + __popc(bal & ((1u << lane) - 1u))] =
+                                (int16_t)p;
+                    }
+                }
             }
             if (threadIdx.x == 0) {
                 const PairRec rc = A.rec[tau * E + sg];
@@ -234,6 +258,7 @@ __global__ void __launch_bounds__(N32_THREADS) near32_kernel(const NearArgs A, c
 void launch_near32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st) {
     int mx = 0;
     for (int k = 1; k <= 3; ++k) mx = a.ss_npp[k] > mx ? a.ss_npp[k] : mx;
+
     const size_t smem = (size_t)mx * sizeof(NearPt32) + ((size_t)mx * sizeof(int16_t) + 15) / 16 * 16;
     cudaFuncSetAttribute(near32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     near32_kernel<<<grid, N32_THREADS, smem, st>>>(a, c32, mx);
