@@ -1377,7 +1377,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
         na.far_spec = (double *)A->dense_spec.p;
         na.smask = (const uint8_t *)A->wsmask.p;
         na.rule_w64 = (const double *)A->rule_w64.p; na.rule_l64 = (const double *)A->rule_l64.p;
-        const int grid = (int)std::min<int64_t>(na.ncolor, (int64_t)2 * nsm);
+        const int grid = (int)std::min<int64_t>(na.ncolor, (int64_t)(A->fp64 ? 2 : 3) * nsm);
         if (grid > 0) {
             if (A->fp64) launch_near(na, grid, st);
             else launch_near32(na, A->c32, grid, st);
