@@ -6,6 +6,8 @@
 
 #include <type_traits>
 
+#include <cstddef>
+
 #include "tdbem_internal.h"
 
 namespace tdbem {
@@ -321,7 +323,25 @@ void launch_gpair_bounds(const Geo &g, double2 *out, cudaStream_t st) {
 // --------------------------------------------------- vertex-pair windows
 // Window of vertex pair (l, j): union over tau in star(l), sigma in star(j)
 // of the element-pair lag ranges (an interval, since both stars are
-// connected). Layout [c][l][j]; an empty window has dlo > dhi.
+// connected). Layout [c][l][j]; an empty window has dlo > dhi. A thread
+// keeps the first VW_STAR triangles of star(j) in registers and reads each
+// record as one aligned 16-byte load, all loads of one tau issued together;
+// stars with more triangles finish in a loop.
+constexpr int VW_STAR = 8;
+static_assert(offsetof(PairRec, lo) == 0 && offsetof(PairRec, cnt) == 6 && offsetof(PairRec, smask) == 9,
+              "vw_add unpacks PairRec by these offsets");
+
+__device__ __forceinline__ void vw_add(const int4 v, int (&lo)[3], int (&hi)[3], unsigned &sm) {
+    // PairRec: lo[3] (int16), cnt[3] (uint8), smask, adj, pad
+    const int l0 = (int)(short)(v.x & 0xffff), l1 = (int)(short)((unsigned)v.x >> 16);
+    const int l2 = (int)(short)(v.y & 0xffff);
+    const int c0 = ((unsigned)v.y >> 16) & 0xff, c1 = ((unsigned)v.y >> 24) & 0xff, c2 = v.z & 0xff;
+    if (c0) { lo[0] = min(lo[0], l0); hi[0] = max(hi[0], l0 + c0 - 1); }
+    if (c1) { lo[1] = min(lo[1], l1); hi[1] = max(hi[1], l1 + c1 - 1); }
+    if (c2) { lo[2] = min(lo[2], l2); hi[2] = max(hi[2], l2 + c2 - 1); }
+    sm |= ((unsigned)v.z >> 8) & 0xff;
+}
+
 __global__ void vertex_windows_kernel(Geo g, const PairRec *rec, int16_t *dlo, int16_t *dhi,
                                       uint8_t *smask, int KW, int *status) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -329,14 +349,19 @@ __global__ void vertex_windows_kernel(Geo g, const PairRec *rec, int16_t *dlo, i
     if (j >= g.M) return;
     int lo[3] = {32767, 32767, 32767}, hi[3] = {-32768, -32768, -32768};
     unsigned sm = 0;
+    const int64_t y0 = g.vt_ptr[j], ny = g.vt_ptr[j + 1] - y0;
+    int sig[VW_STAR];
+#pragma unroll
+    for (int y = 0; y < VW_STAR; ++y) sig[y] = y < ny ? g.vt_tri[y0 + y] : 0;
+    const int4 *R = reinterpret_cast<const int4 *>(rec);
     for (int64_t x = g.vt_ptr[l]; x < g.vt_ptr[l + 1]; ++x) {
-        const int64_t tau = g.vt_tri[x];
-        for (int64_t y = g.vt_ptr[j]; y < g.vt_ptr[j + 1]; ++y) {
-            const PairRec r = rec[tau * g.E + g.vt_tri[y]];
-            for (int c = 0; c < 3; ++c)
-                if (r.cnt[c]) { lo[c] = min(lo[c], (int)r.lo[c]); hi[c] = max(hi[c], r.lo[c] + r.cnt[c] - 1); }
-            sm |= r.smask;
-        }
+        const int4 *row = R + (int64_t)g.vt_tri[x] * g.E;
+        int4 v[VW_STAR];
+#pragma unroll
+        for (int y = 0; y < VW_STAR; ++y) v[y] = y < ny ? __ldg(row + sig[y]) : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int y = 0; y < VW_STAR; ++y) vw_add(v[y], lo, hi, sm);  // an empty record adds nothing
+        for (int64_t y = VW_STAR; y < ny; ++y) vw_add(__ldg(row + g.vt_tri[y0 + y]), lo, hi, sm);
     }
     const int64_t MM = g.M * g.M;
     for (int c = 0; c < 3; ++c) {

@@ -14,10 +14,13 @@ __device__ static double right_end(const double *t, int N, int i) { return i == 
 
 // psi_{k,i}(r) and psi~_{k,i}(r) of Eq. psis: integrate over the overlap of
 // the test support and the shifted trial support, split at the interior
-// breakpoints t_k and t_i + r, composite Gauss-Legendre on each piece.
-__device__ static void psi_direct(int bkind, const double *t, int N, int kb, int m2, int ib, int m1, double r,
-                                  const double *gx, const double *gw, int gn, int gsub,
-                                  double &psi, double &psit) {
+// breakpoints t_k and t_i + r, composite Gauss-Legendre on each piece. One
+// warp evaluates one sample: lane L takes the nodes L, L + 32, ... of each
+// piece (sub-interval-major), and the partial sums are added across the warp
+// in a fixed order, so every lane returns the same values on every run.
+__device__ static void psi_direct_warp(int bkind, const double *t, int N, int kb, int m2, int ib, int m1, double r,
+                                       const double *gx, const double *gw, int gn, int gsub, int lane, double &psi,
+                                       double &psit) {
     psi = 0.0; psit = 0.0;
     const double lo = fmax(left_end(t, N, kb), left_end(t, N, ib) + r);
     const double hi = fmin(right_end(t, N, kb), right_end(t, N, ib) + r);
@@ -30,43 +33,52 @@ __device__ static void psi_direct(int bkind, const double *t, int N, int kb, int
     br[nb++] = hi;
     if (nb == 4 && br[1] > br[2]) { double x = br[1]; br[1] = br[2]; br[2] = x; }
     double s0 = 0.0, s1 = 0.0;
+    const int nq = gsub * gn;
     for (int p = 0; p + 1 < nb; ++p) {
         const double a = br[p], w = (br[p + 1] - br[p]) / gsub;
         if (!(w > 0.0)) continue;
-        for (int q = 0; q < gsub; ++q) {
-            const double a0 = a + q * w;
-            for (int g = 0; g < gn; ++g) {
-                const double tt = a0 + w * gx[g];
-                double bk[3], bi[3];
-                basis_m(bkind, t, N, kb, m2, tt, bk);
-                basis_m(bkind, t, N, ib, m1, tt - r, bi);
-                s0 += w * gw[g] * bi[2] * bk[1];
-                s1 += w * gw[g] * bi[0] * bk[1];
-            }
+        for (int e = lane; e < nq; e += 32) {
+            const int q = e / gn, g = e - q * gn;
+            const double tt = (a + q * w) + w * gx[g];
+            double bk[3], bi[3];
+            basis_m(bkind, t, N, kb, m2, tt, bk);
+            basis_m(bkind, t, N, ib, m1, tt - r, bi);
+            s0 += w * gw[g] * bi[2] * bk[1];
+            s1 += w * gw[g] * bi[0] * bk[1];
         }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     psi = s0;
     psit = s1;
 }
 
-// One thread per (sub-panel, Chebyshev node). Sub-panel p covers
-// r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]); with pdr given, its
-// width is pdr[p] instead (uneven panels of a graded grid); with pm2, pm1
-// given, the block's test and trial temporal orders (else 0).
+// One warp per (sub-panel, Chebyshev node), so that the few hundred samples
+// of a table spread over every SM (the FP64 quadrature is the cost). Sub-panel
+// p covers r in [r0[p], r0[p] + dr] of the block (kb[p], ib[p]); with pdr
+// given, its width is pdr[p] instead (uneven panels of a graded grid); with
+// pm2, pm1 given, the block's test and trial temporal orders (else 0).
 __global__ void psi_samples_kernel(int bkind, const double *t, int N, const int *pkb, const int *pib,
                                    const int *pm2, const int *pm1, const double *pr0, double dr, const double *pdr,
                                    int total, const double *gx, const double *gw, int gn, int gsub,
                                    double *samples) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= total * NCHEB) return;
-    const int p = id / NCHEB, m = id % NCHEB;
+    const int64_t id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (id >= (int64_t)total * NCHEB) return;
+    const int p = (int)(id / NCHEB), m = (int)(id % NCHEB);
     const double xm = cos(M_PI * (m + 0.5) / NCHEB);
     const double w = pdr ? pdr[p] : dr;
     const double r = pr0[p] + 0.5 * w * (xm + 1.0);
     double a, b;
-    psi_direct(bkind, t, N, pkb[p], pm2 ? pm2[p] : 0, pib[p], pm1 ? pm1[p] : 0, r, gx, gw, gn, gsub, a, b);
-    samples[2 * id + 0] = a;
-    samples[2 * id + 1] = b;
+    psi_direct_warp(bkind, t, N, pkb[p], pm2 ? pm2[p] : 0, pib[p], pm1 ? pm1[p] : 0, r, gx, gw, gn, gsub, lane, a,
+                    b);
+    if (lane == 0) {
+        samples[2 * id + 0] = a;
+        samples[2 * id + 1] = b;
+    }
 }
 
 // c_n = (2/K) sum_m f(x_m) cos(n pi (m + 1/2)/K), c_0 halved, K = NCHEB; the
@@ -91,8 +103,8 @@ void launch_psi_samples(int bkind, const double *t, int N, const int *panel_clas
                         int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                         double *samples, cudaStream_t st) {
     (void)panel_class; (void)S;
-    const int n = total_sub * NCHEB;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, nullptr, nullptr,
+    const int64_t n = (int64_t)total_sub * NCHEB * 32;
+    psi_samples_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, nullptr, nullptr,
                                                        panel_r0, panel_dr, nullptr, total_sub, gl_x, gl_w, gl_n,
                                                        gl_sub, samples);
 }
@@ -101,9 +113,9 @@ void launch_psi_samples_var(int bkind, const double *t, int N, const int *panel_
                             const int *panel_m2, const int *panel_m1, const double *panel_r0, const double *panel_dr,
                             int total_sub, const double *gl_x, const double *gl_w, int gl_n, int gl_sub,
                             double *samples, cudaStream_t st) {
-    const int n = total_sub * NCHEB;
+    const int64_t n = (int64_t)total_sub * NCHEB * 32;
     if (n <= 0) return;
-    psi_samples_kernel<<<(n + 127) / 128, 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_m2, panel_m1,
+    psi_samples_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(bkind, t, N, panel_kb, panel_ib, panel_m2, panel_m1,
                                                        panel_r0, 0.0, panel_dr, total_sub, gl_x, gl_w, gl_n, gl_sub,
                                                        samples);
 }
