@@ -1139,6 +1139,13 @@ static void block_run(int64_t k, int64_t i, int64_t N, int32_t &k0, int32_t &i0,
     else if (k == 1 && i == 2) cnt = (int32_t)(N - 3);
 }
 
+// widest lag range of a lag class: the CSR fill keeps one position per lag
+static int fill_lag_span(const tdbem_asm *A) {
+    int n = 1;
+    for (int c = 0; c < NLAG; ++c) n = std::max(n, A->lag_base[c + 1] - A->lag_base[c]);
+    return n;
+}
+
 static tdbem_status plan_matvec(tdbem_asm &A, cudaStream_t st) {
     const int64_t N = A.tg->N, M = A.mesh->M, P1 = A.tg->p + 1, L = N * P1;
     const size_t nb = A.blocks.size();
@@ -1382,7 +1389,7 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
             if (A->fp64) launch_near(na, grid, st);
             else launch_near32(na, A->c32, grid, st);
             // mixed: the far pairs of the special blocks, FP64 (the FP32 kernel skips them)
-            if (!A->fp64) launch_farspec(na, (int)std::min<int64_t>(na.ncolor, (int64_t)8 * nsm), st);
+            if (!A->fp64) launch_farspec32(na, A->c32, (int)std::min<int64_t>(na.ncolor, (int64_t)8 * nsm), st);
         }
     }
     CUDA_TRY(cudaGetLastError());
@@ -1401,13 +1408,13 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                     (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
                     (const int *)A->blk_of_spec_d.p, nullptr, nullptr, (const int64_t *)A->rp_far.p,
                     (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, (const double *)A->dense.p,
-                    (const double *)A->dense_spec.p, A->val_far.p, A->KW, 0, A->fp64, st);
+                    (const double *)A->dense_spec.p, A->val_far.p, A->KW, 0, A->fp64, fill_lag_span(A), st);
         launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
                     (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
                     (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
                     (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
                     (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true,
-                    st);
+                    fill_lag_span(A), st);
         CUDA_TRY(cudaGetLastError());
         tdbem_status ts = build_toeplitz(A, true, st);
         if (ts) return ts;
@@ -1445,12 +1452,12 @@ static tdbem_status assemble_body(tdbem_asm *A, cudaStream_t st, bool capture) {
                 (const int *)A->blk_of_spec_d.p, nullptr, nullptr, (const int64_t *)A->rp_far.p,
                 (const int64_t *)A->off_far_d.p, (int32_t *)A->col_far.p, (const double *)A->dense.p,
                 (const double *)A->dense_spec.p, A->val_far.p,
-                A->KW, 0, A->fp64, st);
+                A->KW, 0, A->fp64, fill_lag_span(A), st);
     launch_fill(M, (const int16_t *)A->wdlo.p, (const int16_t *)A->wdhi.p, (const uint8_t *)A->wsmask.p,
                 (const int *)A->cls_dlo_d.p, (const int *)A->blk_of_lag_d.p, (const int *)A->lag_base_d.p,
                 (const int *)A->blk_of_spec_d.p, (const int64_t *)A->nbr_ptr.p, (const int32_t *)A->nbr.p,
                 (const int64_t *)A->rp_near.p, (const int64_t *)A->off_near_d.p, (int32_t *)A->col_near.p,
-                (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, st);
+                (const double *)A->ndense.p, (const double *)A->ndense_spec.p, A->val_near.p, A->KW, m.NB, true, fill_lag_span(A), st);
     CUDA_TRY(cudaGetLastError());
     if ((s = build_toeplitz(A, false, st))) return s;
     CUDA_TRY(mark(4));

@@ -175,132 +175,6 @@ near_kernel(const NearArgs A) {
     }
 }
 
-// Special blocks (single blocks of the first / last time functions, support
-// near r = 0 or near the corner lag) for element pairs WITHOUT a shared
-// vertex, in FP64 with the 7-point rule on both triangles; used by the mixed
-// path, whose FP32 kernel evaluates only the three lag classes. One CTA per
-// test triangle of the current colour scans its pair records in trial order;
-// its four warps take the qualifying pairs four at a time (lanes over the 49
-// point pairs), and warp 0 adds their values into the far special-block
-// windows in list order.
-constexpr int FS_THREADS = 128;
-constexpr int FS_WARPS = FS_THREADS / 32;
-__global__ void __launch_bounds__(FS_THREADS)
-farspec_kernel(const NearArgs A) {
-    __shared__ int list[FS_THREADS];
-    __shared__ int nlist;
-    __shared__ double fs_val[FS_WARPS][NSPEC][9];  // one list entry per warp: its special-block values
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const Geo &g = A.g;
-    const int64_t M = g.M, E = g.E, MM = M * M;
-    const double inv_dt = A.lt.inv_dt;
-    const int S = A.S;
-    for (int64_t ti = blockIdx.x; ti < A.ncolor; ti += gridDim.x) {
-        const int64_t tau = A.color_tris[ti];
-        for (int64_t b0 = 0; b0 < E; b0 += FS_THREADS) {
-            // ordered compaction of the qualifying trial triangles of this slice
-            const int64_t sg = b0 + threadIdx.x;
-            PairRec rc{};
-            bool need = false;
-            if (sg < E) {
-                rc = A.rec[tau * E + sg];
-                need = rc.adj == 0 && rc.smask != 0;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, need);
-            __shared__ int wcount[FS_THREADS / 32];
-            if (lane == 0) wcount[w] = __popc(bal);
-            __syncthreads();
-            int off = 0;
-            for (int k = 0; k < w; ++k) off += wcount[k];
-            if (need) list[off + __popc(bal & ((1u << lane) - 1u))] = (int)sg;
-            if (threadIdx.x == 0) {
-                int t = 0;
-                for (int k = 0; k < FS_THREADS / 32; ++k) t += wcount[k];
-                nlist = t;
-            }
-            __syncthreads();
-            // four list entries at a time, one per warp, into shared memory;
-            // then warp 0 adds them in list order (entries can share a vertex
-            // pair, so the adds stay in one fixed order)
-            for (int q0 = 0; q0 < nlist; q0 += FS_WARPS) {
-                const int q = q0 + w;
-                if (q < nlist) {
-                    const int64_t s2 = list[q];
-                    const PairRec r2 = A.rec[tau * E + s2];
-                    double nn = 0.0;
-                    for (int d = 0; d < 3; ++d) nn += g.geo64[16 * tau + d] * g.geo64[16 * s2 + d];
-                    const double scale = g.geo64[16 * tau + 3] * g.geo64[16 * s2 + 3] * 0.07957747154594767;
-                    for (int sb = 0; sb < NSPEC; ++sb) {
-                        if (!((r2.smask >> sb) & 1u)) continue;
-                        const int c = NLAG + sb;
-                        const int P = A.lt.P[c], rho = A.lt.rho[c];
-                        int p0 = 0;
-                        for (int x = 0; x < c; ++x) p0 += A.lt.P[x];
-                        double Sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, St = 0.0;
-                        for (int pp = lane; pp < 49; pp += 32) {
-                            const int ix = pp / 7, iy = pp % 7;
-                            double r2s = 0.0;
-                            for (int d = 0; d < 3; ++d) {
-                                const double xd = g.cen[3 * tau + d] + g.dq[(tau * 7 + ix) * 3 + d];
-                                const double yd = g.cen[3 * s2 + d] + g.dq[(s2 * 7 + iy) * 3 + d];
-                                r2s += (xd - yd) * (xd - yd);
-                            }
-                            const double r = sqrt(r2s);
-                            const double v = r * inv_dt - (double)rho;
-                            if (!(v >= 0.0 && v < (double)P)) continue;
-                            const double jf = floor(v);
-                            double u = (v - jf) * S;
-                            const int sub = min((int)floor(u), S - 1);
-                            u -= (double)sub;
-                            const double x = 2.0 * u - 1.0;
-                            const double *cf = A.cheb64 + ((size_t)((p0 + (int)jf) * S + sub) * NCHEB) * 2;
-                            double ps = __ldg(cf) + __ldg(cf + 2) * x, pt = __ldg(cf + 1) + __ldg(cf + 3) * x;
-                            double tm = 1.0, t = x;
-                            const double x2 = x + x;
-                            for (int n = 2; n < NCHEB; ++n) {
-                                const double tn = x2 * t - tm;
-                                tm = t; t = tn;
-                                ps += __ldg(cf + 2 * n) * tn;
-                                pt += __ldg(cf + 2 * n + 1) * tn;
-                            }
-                            const double wgt = A.rule_w64[ix] * A.rule_w64[iy] * scale / r;
-                            for (int a = 0; a < 3; ++a)
-                                for (int b = 0; b < 3; ++b)
-                                    Sab[a][b] += wgt * ps * A.rule_l64[3 * ix + a] * A.rule_l64[3 * iy + b];
-                            St += wgt * pt;
-                        }
-                        for (int a = 0; a < 3; ++a)
-                            for (int b = 0; b < 3; ++b) Sab[a][b] = dsum_warp(Sab[a][b]);
-                        St = dsum_warp(St);
-                        if (lane < 9) {
-                            const int a = lane / 3, b = lane % 3;
-                            const double *ct = g.geo64 + 16 * tau + 4 + 3 * a, *cs = g.geo64 + 16 * s2 + 4 + 3 * b;
-                            const double cc = ct[0] * cs[0] + ct[1] * cs[1] + ct[2] * cs[2];
-                            fs_val[w][sb][lane] = nn * Sab[a][b] + cc * St;
-                        }
-                    }
-                }
-                __syncthreads();
-                if (w == 0 && lane < 9)
-                    for (int k = 0; k < FS_WARPS && q0 + k < nlist; ++k) {
-                        const int64_t s2 = list[q0 + k];
-                        const PairRec r2 = A.rec[tau * E + s2];
-                        const int a = lane / 3, b = lane % 3;
-                        const int64_t l = g.F[3 * tau + a], j = g.F[3 * s2 + b];
-                        for (int sb = 0; sb < NSPEC; ++sb)
-                            if (((r2.smask >> sb) & 1u) && ((A.smask[l * M + j] >> sb) & 1u))
-                                A.far_spec[sb * MM + l * M + j] += fs_val[k][sb][lane];
-                    }
-                __syncthreads();
-            }
-            __syncthreads();
-        }
-    }
-}
-
-void launch_farspec(const NearArgs &a, int grid, cudaStream_t st) {
-    farspec_kernel<<<grid, FS_THREADS, 0, st>>>(a);
-}
 
 void launch_near(const NearArgs &a, int grid, cudaStream_t st) {
     int mx = 0;

@@ -255,6 +255,187 @@ __global__ void __launch_bounds__(N32_THREADS, 3) near32_kernel(const NearArgs A
     }
 }
 
+// Far element pairs (no shared vertex) that reach a special block, with the
+// 7-point rule on both triangles, in the precision scheme of this file:
+// per point pair the distance r, q = r / dt and the factor
+// |tau||sigma| / (4 pi r) in FP64, once for every special block; per
+// (point pair, special block) psi and psi~ from the FP32 tables with the
+// residuals of the leading coefficients; the rule products
+// w_x w_y lambda_a(x) lambda_b(y) and w_x w_y are FP32 pairs (their
+// rounding would otherwise be one bias shared by every element pair), the
+// nine S_ab and S~ are accumulated as FP32 pairs and added across the warp in
+// FP64. One CTA per test triangle of the current colour. Its four warps scan
+// the pair records of one quarter of the trial triangles each, in trial
+// order, into their own lists (no CTA barrier while scanning; a round ends
+// when a list could overflow, or at the end of the row). The concatenated
+// lists are then taken four entries at a time, one per warp (lanes over the
+// 49 point pairs), and warp 0 adds their values into the far special-block
+// windows in list order: the order depends on the data only, so the sums
+// repeat exactly.
+constexpr int FS32_WARPS = 4;
+constexpr int FS32_THREADS = FS32_WARPS * 32;
+constexpr int FS32_LIST = 128;
+__global__ void __launch_bounds__(FS32_THREADS) farspec32_kernel(const NearArgs A, const ChebF32 C) {
+    __shared__ float2 cs[TOTAL_PANELS][NCHEB];
+    __shared__ float2 clo[TOTAL_PANELS][NCHEB_LO];
+    __shared__ float2 gw[49][10];  // (hi, lo) of w_x w_y lambda_a lambda_b, (a, b) row-major, then w_x w_y
+    __shared__ int list[FS32_WARPS][FS32_LIST];
+    __shared__ int wcount[FS32_WARPS];
+    __shared__ double fs_val[FS32_WARPS][NSPEC][9];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Geo &g = A.g;
+    const int64_t M = g.M, E = g.E, MM = M * M;
+    const double inv_dt = A.lt.inv_dt;
+    for (int i = threadIdx.x; i < TOTAL_PANELS * NCHEB; i += FS32_THREADS) {
+        const int p = i / NCHEB, n = i % NCHEB;
+        cs[p][n] = make_float2(C.c[p][n][0], C.c[p][n][1]);
+    }
+    for (int i = threadIdx.x; i < TOTAL_PANELS * NCHEB_LO; i += FS32_THREADS) {
+        const int p = i / NCHEB_LO, n = i % NCHEB_LO;
+        clo[p][n] = make_float2(C.lo[p][n][0], C.lo[p][n][1]);
+    }
+    for (int i = threadIdx.x; i < 49 * 10; i += FS32_THREADS) {
+        const int pp = i / 10, k = i % 10, ix = pp / 7, iy = pp % 7;
+        double v = A.rule_w64[ix] * A.rule_w64[iy];
+        if (k < 9) v *= A.rule_l64[3 * ix + k / 3] * A.rule_l64[3 * iy + k % 3];
+        const float hi = (float)v;
+        gw[pp][k] = make_float2(hi, (float)(v - (double)hi));
+    }
+    __syncthreads();
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t qlen = (E + FS32_WARPS - 1) / FS32_WARPS;
+    const int64_t lo_w = min(E, w * qlen), hi_w = min(E, lo_w + qlen);
+    for (int64_t ti = blockIdx.x; ti < A.ncolor; ti += gridDim.x) {
+        const int64_t tau = A.color_tris[ti];
+        int64_t pos = lo_w;
+        while (__syncthreads_or(pos < hi_w)) {
+            int n = 0;
+            while (pos < hi_w && n + 32 <= FS32_LIST) {
+                const int64_t sg = pos + lane;
+                bool need = false;
+                if (sg < hi_w) {
+                    const PairRec rc = A.rec[tau * E + sg];
+                    need = rc.adj == 0 && rc.smask != 0;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, need);
+                if (need) list[w][n + __popc(bal & lt_mask)] = (int)sg;
+                n += __popc(bal);
+                pos += 32;
+            }
+            if (lane == 0) wcount[w] = n;
+            __syncthreads();
+            int nlist = 0;
+            for (int k = 0; k < FS32_WARPS; ++k) nlist += wcount[k];
+            auto entry = [&](int q) {
+                int k = 0;
+                while (q >= wcount[k]) q -= wcount[k++];
+                return list[k][q];
+            };
+            for (int q0 = 0; q0 < nlist; q0 += FS32_WARPS) {
+                const int q = q0 + w;
+                if (q < nlist) {
+                    const int64_t s2 = entry(q);
+                    const PairRec r2 = A.rec[tau * E + s2];
+                    double nn = 0.0;
+                    for (int d = 0; d < 3; ++d) nn += g.geo64[16 * tau + d] * g.geo64[16 * s2 + d];
+                    const double scale = g.geo64[16 * tau + 3] * g.geo64[16 * s2 + 3] * 0.07957747154594767;
+                    // the lane's point pairs pp = lane, lane + 32: q and |tau||sigma| / (4 pi r)
+                    double qv[2] = {-1.0, -1.0};
+                    float sw[2] = {0.f, 0.f};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int pp = lane + 32 * h;
+                        if (pp >= 49) continue;
+                        const int ix = pp / 7, iy = pp % 7;
+                        double r2s = 0.0;
+                        for (int d = 0; d < 3; ++d) {
+                            const double xd = g.cen[3 * tau + d] + g.dq[(tau * 7 + ix) * 3 + d];
+                            const double yd = g.cen[3 * s2 + d] + g.dq[(s2 * 7 + iy) * 3 + d];
+                            r2s += (xd - yd) * (xd - yd);
+                        }
+                        const double r = sqrt(r2s);
+                        qv[h] = r * inv_dt;
+                        sw[h] = (float)(scale / r);
+                    }
+                    for (int sb = 0; sb < NSPEC; ++sb) {
+                        if (!((r2.smask >> sb) & 1u)) continue;
+                        const int c = NLAG + sb;
+                        const int P = A.lt.P[c], rho = A.lt.rho[c];
+                        int p0 = 0;
+                        for (int x = 0; x < c; ++x) p0 += A.lt.P[x];
+                        float Sh[9], Sl[9], Th = 0.f, Tl = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) Sh[k] = Sl[k] = 0.f;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int pp = lane + 32 * h;
+                            if (pp >= 49) continue;
+                            const double v = qv[h] - (double)rho;
+                            if (!(v >= 0.0 && v < (double)P)) continue;
+                            const double jf = floor(v);
+                            const int j = (int)jf;
+                            const float x = (float)(2.0 * (v - jf) - 1.0), x2 = x + x;
+                            const float2 *cf = cs[p0 + j];
+                            const float2 *lo = clo[p0 + j];
+                            float ps = fmaf(cf[1].x, x, cf[0].x), pt = fmaf(cf[1].y, x, cf[0].y);
+                            float tm = 1.f, tc = x, t2 = 0.f, t3 = 0.f;
+#pragma unroll
+                            for (int nn2 = 2; nn2 < NCHEB; ++nn2) {
+                                const float tn = fmaf(x2, tc, -tm);
+                                tm = tc;
+                                tc = tn;
+                                if (nn2 == 2) t2 = tn;
+                                if (nn2 == 3) t3 = tn;
+                                ps = fmaf(cf[nn2].x, tn, ps);
+                                pt = fmaf(cf[nn2].y, tn, pt);
+                            }
+                            ps += fmaf(lo[3].x, t3, fmaf(lo[2].x, t2, fmaf(lo[1].x, x, lo[0].x)));
+                            pt += fmaf(lo[3].y, t3, fmaf(lo[2].y, t2, fmaf(lo[1].y, x, lo[0].y)));
+                            const float s = sw[h];
+#pragma unroll
+                            for (int k = 0; k < 9; ++k) {
+                                const float2 gk = gw[pp][k];
+                                n32_two_sum(Sh[k], Sl[k], ps * fmaf(s, gk.y, s * gk.x));
+                            }
+                            const float2 gt = gw[pp][9];
+                            n32_two_sum(Th, Tl, pt * fmaf(s, gt.y, s * gt.x));
+                        }
+                        double Sab[9];
+#pragma unroll
+                        for (int k = 0; k < 9; ++k) Sab[k] = n32_dsum_warp((double)Sh[k] + (double)Sl[k]);
+                        const double St = n32_dsum_warp((double)Th + (double)Tl);
+                        if (lane < 9) {
+                            const int a = lane / 3, b = lane % 3;
+                            const double *ct = g.geo64 + 16 * tau + 4 + 3 * a, *cs2 = g.geo64 + 16 * s2 + 4 + 3 * b;
+                            const double cc = ct[0] * cs2[0] + ct[1] * cs2[1] + ct[2] * cs2[2];
+                            double Sl9 = Sab[0];
+#pragma unroll
+                            for (int k = 1; k < 9; ++k) Sl9 = lane == k ? Sab[k] : Sl9;
+                            fs_val[w][sb][lane] = nn * Sl9 + cc * St;
+                        }
+                    }
+                }
+                __syncthreads();
+                if (w == 0 && lane < 9)
+                    for (int k = 0; k < FS32_WARPS && q0 + k < nlist; ++k) {
+                        const int64_t s2 = entry(q0 + k);
+                        const PairRec r2 = A.rec[tau * E + s2];
+                        const int a = lane / 3, b = lane % 3;
+                        const int64_t l = g.F[3 * tau + a], j = g.F[3 * s2 + b];
+                        for (int sb = 0; sb < NSPEC; ++sb)
+                            if (((r2.smask >> sb) & 1u) && ((A.smask[l * M + j] >> sb) & 1u))
+                                A.far_spec[sb * MM + l * M + j] += fs_val[k][sb][lane];
+                    }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+void launch_farspec32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st) {
+    farspec32_kernel<<<grid, FS32_THREADS, 0, st>>>(a, c32);
+}
+
 void launch_near32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st) {
     int mx = 0;
     for (int k = 1; k <= 3; ++k) mx = a.ss_npp[k] > mx ? a.ss_npp[k] : mx;

@@ -6,6 +6,7 @@
 
 #include <type_traits>
 
+#include <algorithm>
 #include <cstddef>
 
 #include "tdbem_internal.h"
@@ -511,9 +512,12 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                             const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                             const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
                             const int64_t *row_ptr, const int64_t *blk_off, int32_t *col,
-                            const double *dense, const double *dense_spec, T *val, int KW, int NB) {
-    __shared__ int cur[RC_WARPS][MAXLAG];
+                            const double *dense, const double *dense_spec, T *val, int KW, int NB, int nxmax) {
+    // per warp: the next CSR position of row l in the block of every lag of
+    // the class (block offset + row start + entries written so far)
+    extern __shared__ int64_t fill_pos[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t *cur = fill_pos + (size_t)w * nxmax;
     const int64_t item = blockIdx.x * (int64_t)RC_WARPS + w;
     if (item >= 4 * M) return;
     const bool nearp = nbr_ptr != nullptr;
@@ -523,7 +527,11 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
     const int64_t k0 = nearp ? nbr_ptr[l] : 0, k1 = nearp ? nbr_ptr[l + 1] : M;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (c < 3) {
-        for (int x = lane; x < MAXLAG; x += 32) cur[w][x] = 0;
+        const int nx = lag_base[c + 1] - lag_base[c];
+        for (int x = lane; x < nx; x += 32) {
+            const int blk = blk_of_lag[lag_base[c] + x];
+            cur[x] = blk >= 0 ? blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] : 0;
+        }
         __syncwarp();
         for (int64_t kb = k0; kb < k1; kb += 32) {
             const int64_t k = kb + lane;
@@ -541,10 +549,8 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
                 if (!bal) continue;
                 const int x = d - cls_dlo[c];
-                const int blk = blk_of_lag[lag_base[c] + x];
                 if (in) {
-                    const int64_t pos = blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] + cur[w][x] +
-                                        __popc(bal & lt_mask);
+                    const int64_t pos = cur[x] + __popc(bal & lt_mask);
                     col[pos] = (int32_t)j;
                     const int64_t src = nearp ? ((c * M + l) * NB + (k - k0)) : (c * MM + l * M + j);
                     if constexpr (std::is_same<T, float>::value) {
@@ -556,12 +562,17 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                     }
                 }
                 __syncwarp();
-                if (lane == 0) cur[w][x] += __popc(bal);
+                if (lane == 0) cur[x] += __popc(bal);
                 __syncwarp();
             }
         }
     } else {
-        int64_t sc[NSPEC] = {0, 0, 0, 0, 0};
+        int64_t sc[NSPEC];
+#pragma unroll
+        for (int s = 0; s < NSPEC; ++s) {
+            const int blk = blk_of_spec[s];
+            sc[s] = blk >= 0 ? blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] : 0;
+        }
         for (int64_t kb = k0; kb < k1; kb += 32) {
             const int64_t k = kb + lane;
             const bool ok = k < k1;
@@ -573,8 +584,7 @@ __global__ void fill_kernel(int64_t M, const int16_t *dlo, const int16_t *dhi, c
                 if (!bal) continue;
                 const int blk = blk_of_spec[s];
                 if (in && blk >= 0) {
-                    const int64_t pos = blk_off[blk] + row_ptr[(int64_t)blk * (M + 1) + l] + sc[s] +
-                                        __popc(bal & lt_mask);
+                    const int64_t pos = sc[s] + __popc(bal & lt_mask);
                     col[pos] = (int32_t)j;
                     const int64_t src = nearp ? ((s * M + l) * NB + (k - k0)) : (s * MM + l * M + j);
                     val[pos] = (T)dense_spec[src];
@@ -589,16 +599,23 @@ void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_
                  const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                  const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
                  const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const double *dense,
-                 const double *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st) {
+                 const double *dense_spec, void *val, int KW, int NB, bool fp64, int nxmax, cudaStream_t st) {
     const unsigned grid = (unsigned)((4 * M + RC_WARPS - 1) / RC_WARPS);
-    if (fp64)
-        fill_kernel<double><<<grid, RC_WARPS * 32, 0, st>>>(
+    nxmax = std::max(nxmax, 1);
+    const size_t smem = (size_t)RC_WARPS * nxmax * sizeof(int64_t);
+    if (fp64) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(fill_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fill_kernel<double><<<grid, RC_WARPS * 32, smem, st>>>(
             M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
-            blk_off, col, dense, dense_spec, (double *)val, KW, NB);
-    else
-        fill_kernel<float><<<grid, RC_WARPS * 32, 0, st>>>(
+            blk_off, col, dense, dense_spec, (double *)val, KW, NB, nxmax);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(fill_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        fill_kernel<float><<<grid, RC_WARPS * 32, smem, st>>>(
             M, dlo, dhi, smask, cls_dlo, blk_of_lag, lag_base, blk_of_spec, nbr_ptr, nbr, row_ptr,
-            blk_off, col, dense, dense_spec, (float *)val, KW, NB);
+            blk_off, col, dense, dense_spec, (float *)val, KW, NB, nxmax);
+    }
 }
 
 }  // namespace tdbem

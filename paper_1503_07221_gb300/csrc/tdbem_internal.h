@@ -155,7 +155,7 @@ void launch_fill(int64_t M, const int16_t *dlo, const int16_t *dhi, const uint8_
                  const int *cls_dlo, const int *blk_of_lag, const int *lag_base,
                  const int *blk_of_spec, const int64_t *nbr_ptr, const int32_t *nbr,
                  const int64_t *row_ptr, const int64_t *blk_off, int32_t *col, const double *dense,
-                 const double *dense_spec, void *val, int KW, int NB, bool fp64, cudaStream_t st);
+                 const double *dense_spec, void *val, int KW, int NB, bool fp64, int nxmax, cudaStream_t st);
 
 // far.cu
 struct FarArgs {
@@ -231,8 +231,10 @@ struct NearArgs {
 void launch_near(const NearArgs &a, int grid, cudaStream_t st);
 // near32.cu: the same near field with psi, psi~ in FP32 (mixed path)
 void launch_near32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st);
-// far element pairs that reach a special block, FP64 7-point rule
-void launch_farspec(const NearArgs &a, int grid, cudaStream_t st);
+// far element pairs that reach a special block, 7-point rule, psi and psi~
+// in FP32 with FP32-pair sums (mixed path; the FP64 far kernel handles them
+// itself)
+void launch_farspec32(const NearArgs &a, const ChebF32 &c32, int grid, cudaStream_t st);
 
 // matvec.cu: one unique block and the diagonal run of block positions
 // (k0 + p, i0 + p), p < cnt, that it stands for (Eq. relationAtildeBlock)
