@@ -689,7 +689,8 @@ __device__ __forceinline__ void scatter_chunk32(const FarArgs &A, const Setup32 
 }
 
 // Special blocks (cell 0 and the first/last-row corner) are not evaluated
-// here: the few far pairs that reach them go through the FP64 pass in near.cu.
+// here: the few far pairs that reach them go through farspec32_kernel
+// (near32.cu), with FP64 distances and FP32-pair sums.
 // Shared memory: two element-pair setups, the thread slots of P1 (reused for
 // the 3x3 values of P2 once they are read), the window starts, the staged
 // chunk plan and lag windows.
