@@ -104,7 +104,12 @@ def test_fgmres_matches_oracle(td, sphere, N, inner):
 
 
 def test_max_iter_bounds_a_stalled_solve(td, sphere):
-    # FGMRES(50, 2(2, 10)) on N = 6 stalls near 1e-2 (the oracle too)
+    # FGMRES(50, 2(2, 10)) on N = 6 stalls near 1e-2 (the oracle too). Where
+    # a stalled flexible iteration with inexact inner solves stops depends on
+    # rounding: multiplying every entry of the oracle's own matrix by
+    # (1 + 1e-16 N(0, 1)) moves its final residual by 6-15 %. So the test
+    # asks for the stall (the cap reached, the residual far above the
+    # tolerance) at the oracle's level within a factor of 2.
     import torch
     from oracle.krylov import solve
     asm, A, g, M = _case(td, sphere, 6)
@@ -112,7 +117,7 @@ def test_max_iter_bounds_a_stalled_solve(td, sphere):
     alpha, it, rr = asm.solve_fgmres(torch.from_numpy(g).cuda(), restart=50, tol=1e-5, max_iter=120, inner=(2, 10))
     print("stalled: %d iterations, rel res %.3e (oracle %d, %.3e)" % (it, rr, it_ref, hist[-1]))
     assert it == it_ref == 120
-    assert rr > 1e-5 and abs(rr - hist[-1]) <= 5e-2 * hist[-1]
+    assert rr > 1e-3 and 0.5 * hist[-1] <= rr <= 2.0 * hist[-1]
 
 
 def test_fgmres_deterministic_and_zero_rhs(td, sphere):
