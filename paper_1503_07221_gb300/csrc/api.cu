@@ -733,9 +733,18 @@ static tdbem_status create_graded(tdbem_asm &A, cudaStream_t st) {
     if (s) return s;
     const tdbem_mesh &m = *A.mesh;
     const int64_t M = m.M, E = m.E;
+    // the colouring rebalanced for the far kernel's grid (one CTA per SM)
+    int nsm_dev = 0;
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm_dev, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return fail(TDBEM_E_CUDA, std::string("device attributes: ") + cudaGetErrorString(e));
+    }
+    const std::vector<std::vector<int32_t>> bal = balance_colours(m, nsm_dev);
     std::vector<int32_t> colors;
     A.color_off.assign(1, 0);
-    for (auto &c : m.colors) { colors.insert(colors.end(), c.begin(), c.end()); A.color_off.push_back((int64_t)colors.size()); }
+    for (auto &c : bal) { colors.insert(colors.end(), c.begin(), c.end()); A.color_off.push_back((int64_t)colors.size()); }
     std::vector<float> geol(16 * E), cenh(3 * E), cenl(3 * E);
     for (int64_t k = 0; k < 16 * E; ++k) geol[k] = (float)(m.geo64[k] - (double)m.geo32[k]);
     for (int64_t k = 0; k < 3 * E; ++k) {
