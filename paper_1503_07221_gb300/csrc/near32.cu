@@ -105,10 +105,11 @@ __global__ void __launch_bounds__(N32_THREADS, 3) near32_kernel(const NearArgs A
                     const double yd = Y[0][d] + yh0 * (Y[1][d] - Y[0][d]) + yh1 * (Y[2][d] - Y[1][d]);
                     r2 += (xd - yd) * (xd - yd);
                 }
-                const double r = sqrt(r2);
-                const double q = r * inv_dt;
+                // 1 / r once (CUDA's FP64 rsqrt, within 1 ulp): r and the weight w / r
+                const double ir = rsqrt(r2);
+                const double q = (r2 * ir) * inv_dt;
                 const double cf = floor(q);
-                const double wgt = rule[5 * p + 4] * scale / r;
+                const double wgt = rule[5 * p + 4] * scale * ir;
                 NearPt32 t;
                 t.x = (float)(2.0 * (q - cf) - 1.0);
                 t.wh = (float)wgt;
@@ -353,9 +354,9 @@ __global__ void __launch_bounds__(FS32_THREADS) farspec32_kernel(const NearArgs 
                             const double yd = g.cen[3 * s2 + d] + g.dq[(s2 * 7 + iy) * 3 + d];
                             r2s += (xd - yd) * (xd - yd);
                         }
-                        const double r = sqrt(r2s);
-                        qv[h] = r * inv_dt;
-                        sw[h] = (float)(scale / r);
+                        const double ir = rsqrt(r2s);  // 1 / r within 1 ulp: r and the weight factor
+                        qv[h] = (r2s * ir) * inv_dt;
+                        sw[h] = (float)(scale * ir);
                     }
                     for (int sb = 0; sb < NSPEC; ++sb) {
                         if (!((r2.smask >> sb) & 1u)) continue;
